@@ -1,0 +1,335 @@
+"""Throughput of Gaussian-random-field sampling on GB300 (fields/s and grid points/s).
+
+One step = one call of grf_sample drawing a batch of 64 FP32 fields of a 2-D
+4096 x 4096 grid on [0,1]^2 (Matern sigma = 1, ell = 0.05, nu = 2.5, Algorithm 2),
+seeds step*64 .. step*64+63 (the 4096^2 workload of the headline metric).
+The 4 GiB output per step is larger than L2, so no flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+instead (one field per step) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fields/s and Gpts/s (2-D 4096², 3-D 256³ FP32) vs FP64 plain; % HBM roofline"
+SHAPE = (4096, 4096)
+BATCH = 64
+SPEC = dict(family="matern", sigma=1.0, ell=0.05, nu=2.5)
+WORKLOAD = "2-D 4096x4096 FP32 Matern(sigma=1, ell=0.05, nu=2.5) on [0,1]^2, Algorithm 2, batch 64, seeds step*64+b"
+PAPER_FIELDS_PER_S = 4.0  # 0.25 s for one 512x512 field on the paper's machine (context only)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _oracle_fields_per_s(nfields: int = 1):
+    """Time the FP64 CPU oracle (as it stands) on `nfields` 4096^2 fields in a child
+    process pinned to one BLAS/OpenMP thread.  Returns (fields/s, seconds, cores)."""
+    code = (
+        "import time, sys\n"
+        "sys.path.insert(0, %r)\n"
+        "from oracle import grf_oracle as O\n"
+        "sp = O.Spectrum(O.MATERN, 1.0, 0.05, 2.5)\n"
+        "t = time.perf_counter()\n"
+        "for b in range(%d): O.alg2_field(%r, (1.0, 1.0), sp, b)\n"
+        "print(time.perf_counter() - t)\n" % (ROOT, nfields, SHAPE))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    dt = float(r.stdout.strip().splitlines()[-1])
+    return nfields / dt, dt, 1
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state worth paying a 4096^2 field for
+    times = []
+    for _ in range(args.steps):
+        _, dt, cores = _oracle_fields_per_s(1)
+        times.append(dt)
+    tot = sum(times)
+    value = args.steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "fields/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD.replace("batch 64", "one field per step"), "impl": "FP64 numpy oracle"},
+        "cpu_baseline": {"value": value, "unit": "fields/s", "cores": cores, "kind": "oracle",
+                         "sample": "one 4096x4096 field per step, FP64 numpy oracle (recursive radix-2 FFT)"},
+        "e2e": {"value": value, "unit": "fields/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpts_per_s": value * SHAPE[0] * SHAPE[1] / 1e9,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _pass_bytes(kind: str, hsize: int, ntot: int) -> int:
+    """Algorithmic HBM bytes of one launch per field: the noise pass writes the
+    complex half spectrum; the c2r pass reads it and writes the real field."""
+    if kind == "noise_columns":
+        return 8 * hsize
+    if kind == "rows_c2r":
+        return 8 * hsize + 4 * ntot
+    return 0
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1105_2737_gb300 import build
+    build()
+    from paper_1105_2737_gb300 import _lib as L
+    from paper_1105_2737_gb300.api import GRF
+
+    g = GRF(SHAPE, (1.0, 1.0), max_batch=BATCH, **SPEC)
+    ntot = SHAPE[0] * SHAPE[1]
+    hsize = SHAPE[0] * (SHAPE[1] // 2 + 1)
+    out = g.empty(BATCH)
+    seed0 = rank * 1_000_000
+    stream = torch.cuda.current_stream()
+
+    def step(i):
+        g.sample(seed=seed0 + i * BATCH, batch=BATCH, out=out)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+
+    # per-launch timing inside the timed region (events on the launching stream)
+    L.grf_plan_timing(g.handle, 16 * args.steps)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for i in range(args.steps):
+            step(args.warmup + i)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    nrec, recs = L.grf_plan_timing_read(g.handle)
+    L.grf_plan_timing(g.handle, 0)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    fields = BATCH * args.steps * ws
+    value = fields / (ms / 1000.0)
+
+    # dominant kernel and its roofline
+    per_kind = {}
+    for kind, t in recs:
+        per_kind.setdefault(kind, []).append(t)
+    dom = max(per_kind, key=lambda k: sum(per_kind[k]))
+    avg_ms = sum(per_kind[dom]) / len(per_kind[dom])
+    peak, peak_src = _peaks()
+    alg_bytes = _pass_bytes(dom, hsize, ntot) * BATCH
+    achieved = alg_bytes / (avg_ms / 1000.0) / 1e9
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tr = json.load(f)
+        ent = tr.get(dom)
+        from paper_1105_2737_gb300.build import _fingerprint
+        if ent and ent.get("fingerprint") == _fingerprint()[:16]:
+            traffic = float(ent["bytes_per_field"]) * BATCH
+    except Exception:
+        traffic = None
+    passes = {k: {"launches": len(v), "avg_ms": sum(v) / len(v),
+                  "GBps_alg": (_pass_bytes(k, hsize, ntot) * BATCH / (sum(v) / len(v) / 1000.0) / 1e9)
+                  if _pass_bytes(k, hsize, ntot) else None} for k, v in per_kind.items()}
+    # BASELINE's per-pass figure: 4 B per point written per HBM pass (P = 2 for 2-D)
+    P = 2
+    per_pass_frac = (fields * ntot * 4 * P) / (ms / 1000.0) / 1e9 / peak / ws
+    strict_frac = (fields * ntot * 4) / (ms / 1000.0) / 1e9 / peak / ws
+
+    # end to end through the public API, fields delivered to pinned host memory
+    host = torch.empty((BATCH,) + SHAPE, dtype=torch.float32, pin_memory=True)
+    g.sample_host(seed=seed0, batch=BATCH, out=host)
+    torch.cuda.synchronize()
+    e_steps = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for i in range(e_steps):
+        g.sample_host(seed=seed0 + i * BATCH, batch=BATCH, out=host)
+    e2e_s = time.perf_counter() - t0
+    e2e_val = BATCH * e_steps / e2e_s
+    if ws > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_val = BATCH * e_steps * ws / float(t.item())
+    del host
+
+    # plain FP64 form on the same GPU, one field per launch sequence
+    del out
+    torch.cuda.empty_cache()
+    g64 = GRF(SHAPE, (1.0, 1.0), precision="fp64", max_batch=1, **SPEC)
+    o64 = g64.empty(1)
+    g64.sample(0, 1, out=o64)
+    torch.cuda.synchronize()
+    n64 = 6
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for i in range(n64):
+        g64.sample(i, 1, out=o64)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    fp64_fields_per_s = n64 / (a0.elapsed_time(a1) / 1000.0)
+    g64.close()
+    del o64
+
+    # secondary workload of the metric: 3-D 256^3 batch 8 (Gaussian, ell = 0.03)
+    g3 = GRF((256, 256, 256), (1.0, 1.0, 1.0), family="gaussian", sigma=1.0, ell=0.03, max_batch=8)
+    o3 = g3.empty(8)
+    for i in range(2):
+        g3.sample(i * 8, 8, out=o3)
+    torch.cuda.synchronize()
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k3 = max(3, args.steps)
+    b0.record(stream)
+    for i in range(k3):
+        g3.sample(i * 8, 8, out=o3)
+    b1.record(stream)
+    torch.cuda.synchronize()
+    ms3 = b0.elapsed_time(b1) / k3
+    fields3 = 8 / (ms3 / 1000.0)
+    g3.close()
+    del o3
+
+    if rank != 0:
+        return
+    cpu_val, cpu_s, cores = _oracle_fields_per_s(1) if not args.no_cpu else (None, None, None)
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": "fields/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": list(SHAPE), "batch_per_gpu": BATCH, "alg": 2,
+                   "l2": "output 4 GiB per step > L2 (no flush needed)", "parallelism": "replicas (seed ranges)"},
+        "gpts_per_s": value * ntot / 1e9,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src + " (hbm_gbs copy)",
+                     "alg_bytes_per_launch": alg_bytes},
+        "per_pass_hbm_frac": per_pass_frac, "strict_hbm_frac": strict_frac, "passes_P": P,
+        "passes": passes,
+        "fp64_plain": {"fields_per_s": fp64_fields_per_s, "ratio_fp32_batched_over_fp64_plain": value / ws / fp64_fields_per_s},
+        "extra_3d_256cubed_batch8": {"fields_per_s": fields3, "gpts_per_s": fields3 * 256 ** 3 / 1e9,
+                                     "ms_per_call": ms3},
+        "e2e": {"value": e2e_val, "unit": "fields/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": BATCH * ntot * 4,
+                "note": "grf_sample_host: seeds passed by value (no input buffers); the 64 fields are copied to pinned host memory, copies overlapped with compute"},
+        "gpu_launches": nrec,
+        "clocks": clocks,
+        "cpu_baseline": ({"value": cpu_val, "unit": "fields/s", "cores": cores, "kind": "oracle",
+                          "sample": "one 4096x4096 field of the same workload, FP64 numpy oracle, %.1f s" % cpu_s}
+                         if cpu_val else None),
+        "paper_context": {"fields_per_s_512sq": PAPER_FIELDS_PER_S, "note": "0.25 s per 512x512 field on an older CPU"},
+    }
+    print(json.dumps(line), flush=True)
+    g.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,818 @@
+// C ABI of the GRF library: plan creation (validation, FP64 table builds,
+// workspace, schedules), sampling (Algorithm 2 and Algorithm 1 of §3),
+// the adjoint with respect to (sigma, ell, nu), and the forward r2c DFT.
+#include "grf.h"
+#include "kernels.h"
+#include "plain64.h"
+#include "batch.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace grf;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+grf_status fail(grf_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+grf_status cuda_fail(cudaError_t e, const char* where) {
+  g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? GRF_ERR_OOM : GRF_ERR_CUDA;
+}
+
+#define GRF_CUDA(call, where)                      \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+  } while (0)
+
+bool is_pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
+int ilog2(int64_t x) {
+  int r = 0;
+  while ((int64_t(1) << r) < x) ++r;
+  return r;
+}
+int64_t next_pow2(int64_t x) {
+  int64_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+// psi(x): recurrence up to x >= 10, then the asymptotic series
+// (Abramowitz & Stegun 6.3.5, 6.3.18).
+double digamma_host(double x) {
+  double acc = 0.0;
+  while (x < 10.0) {
+    acc -= 1.0 / x;
+    x += 1.0;
+  }
+  const double x2 = 1.0 / (x * x);
+  const double series =
+      x2 * (1.0 / 12 - x2 * (1.0 / 120 - x2 * (1.0 / 252 - x2 * (1.0 / 240 - x2 * (1.0 / 132)))));
+  return acc + std::log(x) - 0.5 / x - series;
+}
+
+struct ColSched {
+  int C = 1, P = 16;
+};
+struct RowSched {
+  int C = 1, P = 16;
+};
+
+const size_t kSmemCap = 100 * 1024;
+
+ColSched choose_col(int N, int64_t ncols, int max_threads = 512) {
+  ColSched s;
+  s.P = points_per_thread(N);
+  const int TPT = N / s.P;
+  int C = max_threads / TPT;
+  if (C < 1) C = 1;
+  while (C > 1 && col_smem_bytes(N, C) > kSmemCap) C >>= 1;
+  const int64_t cp = next_pow2(ncols);
+  if (C > cp) C = (int)cp;
+  s.C = C;
+  return s;
+}
+
+RowSched choose_row(int M, int64_t nrows, int max_threads = 512) {
+  RowSched s;
+  s.P = M >= 16 ? 16 : M;
+  const int TPT = M / s.P;
+  int C = max_threads / TPT;
+  if (C < 1) C = 1;
+  while (C > 1 && row_smem_bytes(M, C) > kSmemCap) C >>= 1;
+  const int64_t rp = next_pow2(nrows);
+  if (C > rp) C = (int)rp;
+  s.C = C;
+  return s;
+}
+
+}  // namespace
+
+struct grf_plan_s {
+  int kind = 0;  // 0: one shape; 1: uneven batch
+  int d = 0;
+  int64_t n[3] = {1, 1, 1};
+  double L[3] = {1, 1, 1};
+  grf_spectrum spec{};
+  int alg = 2, prec = 0;
+  int64_t max_batch = 1;
+  int device = 0;
+  double norm_scale = 1.0;
+
+  // geometry
+  int N1 = 1, Nmid = 1, M = 1;
+  int64_t ntot = 0, hsize = 0, fold_size = 0;
+
+  // FP32 tables and workspace
+  float2* tw = nullptr;
+  int twmax = 0;
+  float* stab = nullptr;
+  float* dstab = nullptr;
+  float2* ws = nullptr;
+  int64_t chunk = 1;
+  double* partial = nullptr;
+  int64_t partial_cap = 0;
+  int T = 1;  // 2-D tile of the half-spectrum workspace
+  ColSched colA, colB;
+  RowSched row;
+
+  // FP64 plain form
+  double2* tw64 = nullptr;
+  double* stab64 = nullptr;
+  double2* bufA = nullptr;
+  double2* bufB = nullptr;
+
+  // host delivery
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_done[2] = {nullptr, nullptr};
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr};
+  void* stage[2] = {nullptr, nullptr};
+  int64_t stage_fields = 0;
+
+  int* status = nullptr;  // device status word
+
+  BatchPlan* batch = nullptr;
+
+  // per-launch timing
+  std::vector<cudaEvent_t> tev;
+  std::vector<int> tkind;
+  int64_t tcap = 0, tused = 0;
+};
+
+namespace {
+
+void free_plan(grf_plan p) {
+  if (!p) return;
+  cudaFree(p->tw);
+  cudaFree(p->stab);
+  cudaFree(p->dstab);
+  cudaFree(p->ws);
+  cudaFree(p->partial);
+  cudaFree(p->tw64);
+  cudaFree(p->stab64);
+  cudaFree(p->bufA);
+  cudaFree(p->bufB);
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(p->stage[i]);
+    if (p->ev_done[i]) cudaEventDestroy(p->ev_done[i]);
+    if (p->ev_copied[i]) cudaEventDestroy(p->ev_copied[i]);
+  }
+  if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+  cudaFree(p->status);
+  if (p->batch) batch_plan_free(p->batch);
+  for (cudaEvent_t e : p->tev) cudaEventDestroy(e);
+  delete p;
+}
+
+template <class T>
+cudaError_t dmalloc(T** ptr, size_t count) {
+  if (count == 0) count = 1;
+  return cudaMalloc((void**)ptr, count * sizeof(T));
+}
+
+grf_status validate_spec(const grf_spectrum* spec) {
+  if (!spec) return fail(GRF_ERR_INVALID_ARG, "spec is NULL");
+  if (spec->family < 0 || spec->family > 2) return fail(GRF_ERR_INVALID_ARG, "unknown spectral family");
+  if (!(spec->sigma > 0) || !std::isfinite(spec->sigma)) return fail(GRF_ERR_INVALID_ARG, "sigma must be > 0");
+  if (spec->family <= 1 && (!(spec->ell > 0) || !std::isfinite(spec->ell)))
+    return fail(GRF_ERR_INVALID_ARG, "ell must be > 0");
+  if (spec->family == 0 && (!(spec->nu > 0) || !std::isfinite(spec->nu)))
+    return fail(GRF_ERR_INVALID_ARG, "nu must be > 0");
+  if (spec->family == 2 && (!(spec->m > 0) || spec->k < 1 || spec->l < 1 || spec->n < 1))
+    return fail(GRF_ERR_INVALID_ARG, "paper family needs m > 0 and k, l, n >= 1");
+  return GRF_OK;
+}
+
+SpecParams spec_params(const grf_plan_s* p) {
+  SpecParams sp{};
+  sp.family = p->spec.family;
+  sp.sigma = p->spec.sigma;
+  sp.ell = p->spec.ell;
+  sp.nu = p->spec.nu;
+  sp.m = p->spec.m;
+  sp.k = p->spec.k;
+  sp.l = p->spec.l;
+  sp.n = p->spec.n;
+  sp.scale = p->norm_scale;
+  sp.d = p->d;
+  for (int i = 0; i < 3; ++i) {
+    sp.L[i] = p->L[i];
+    sp.nn[i] = (int)p->n[i];
+  }
+  return sp;
+}
+
+// sum_K S(p_K)/|D| over the full grid, in FP64 on the host (folded, with multiplicities).
+double discrete_sum(const grf_plan_s* p) {
+  const double PI = 3.141592653589793238462643383279502884;
+  const int d = p->d;
+  const grf_spectrum& s = p->spec;
+  double vol = 1.0;
+  for (int i = 0; i < d; ++i) vol *= p->L[i];
+  double c = 0.0;
+  if (s.family == 0)
+    c = std::pow(2.0 * std::sqrt(PI) * s.ell, d) * std::exp(std::lgamma(s.nu + 0.5 * d) - std::lgamma(s.nu));
+  else if (s.family == 1)
+    c = std::pow(2.0 * PI * s.ell * s.ell, 0.5 * d);
+  int64_t F[3] = {1, 1, 1};
+  for (int i = 0; i < d; ++i) F[i] = p->n[i] / 2 + 1;
+  double total = 0.0;
+  for (int64_t a = 0; a < F[0]; ++a)
+    for (int64_t b = 0; b < F[1]; ++b)
+      for (int64_t e = 0; e < F[2]; ++e) {
+        const int64_t f[3] = {a, b, e};
+        double p2 = 0.0, mult = 1.0, s2k = 0.0;
+        for (int i = 0; i < d; ++i) {
+          const double pi = (double)f[i] / p->L[i];
+          p2 += pi * pi;
+          if (s.family == 2) s2k += std::pow(pi, 2.0 * s.k);
+          if (f[i] != 0 && f[i] != p->n[i] / 2) mult *= 2.0;
+        }
+        double S;
+        if (s.family == 0) S = s.sigma * s.sigma * c * std::pow(1.0 + s.ell * s.ell * 4 * PI * PI * p2, -s.nu - 0.5 * d);
+        else if (s.family == 1) S = s.sigma * s.sigma * c * std::exp(-2 * PI * PI * s.ell * s.ell * p2);
+        else S = s.sigma * s.sigma * std::pow(std::pow(s.m, (double)(s.k * s.l)) + std::pow(s2k, (double)s.l), -(double)s.n);
+        total += mult * S / vol;
+      }
+  return total;
+}
+
+grf_status ensure_partial(grf_plan p, int64_t count) {
+  if (count <= p->partial_cap) return GRF_OK;
+  cudaFree(p->partial);
+  p->partial = nullptr;
+  p->partial_cap = 0;
+  GRF_CUDA(dmalloc(&p->partial, (size_t)count * 3), "partial buffer");
+  p->partial_cap = count;
+  return GRF_OK;
+}
+
+HalfGeom half_geom(const grf_plan_s* p, uint64_t seed, int64_t field0) {
+  HalfGeom g{};
+  g.d = p->d;
+  g.N1 = p->N1;
+  g.Nmid = p->Nmid;
+  g.M = p->M;
+  g.Q = (uint32_t)(p->M / 2 + 1);
+  g.seed = seed;
+  g.field0 = field0;
+  g.stab = p->stab;
+  g.dstab = p->dstab;
+  g.inv_sigma = (float)(1.0 / p->spec.sigma);
+  g.alg1_scale = (float)(1.0 / std::sqrt((double)p->ntot));
+  return g;
+}
+
+const float2* twp(const grf_plan_s* p, int len) { return p->tw + len; }
+
+// Column pass along axis 1 (the transform length N1); plane = whole field.
+ColArgs col_axis1(const grf_plan_s* p, const HalfGeom& g, const float2* in, float2* out, int T) {
+  ColArgs a{};
+  a.N = p->N1;
+  a.logN = ilog2(p->N1);
+  a.C = p->colA.C;
+  a.ncols = (int64_t)p->Nmid * (p->M + 1);
+  a.T = T;
+  a.ostride = 0;
+  a.bstride = p->hsize;
+  a.in = in;
+  a.out = out;
+  a.tw = twp(p, p->N1);
+  a.plane_is_k1 = 1;
+  a.g = g;
+  return a;
+}
+
+// Column pass along axis 2 of a 3-D half spectrum (planes = j1 or k1).
+ColArgs col_axis2(const grf_plan_s* p, const HalfGeom& g, const float2* in, float2* out) {
+  ColArgs a{};
+  a.N = p->Nmid;
+  a.logN = ilog2(p->Nmid);
+  a.C = p->colB.C;
+  a.ncols = p->M + 1;
+  a.T = 1;
+  a.ostride = (int64_t)p->Nmid * (p->M + 1);
+  a.bstride = p->hsize;
+  a.in = in;
+  a.out = out;
+  a.tw = twp(p, p->Nmid);
+  a.plane_is_k1 = 0;
+  a.g = g;
+  return a;
+}
+
+RowArgs row_args(const grf_plan_s* p, const HalfGeom& g, int64_t nfields, int T) {
+  RowArgs r{};
+  r.M = p->M;
+  r.logM = ilog2(p->M);
+  r.C = p->row.C;
+  r.rows_per_field = p->ntot / p->n[p->d - 1];
+  r.nrows = nfields * r.rows_per_field;
+  r.T = T;
+  r.twM = twp(p, p->M);
+  r.twN = twp(p, 2 * p->M);
+  r.g = g;
+  return r;
+}
+
+dim3 col_grid(const ColArgs& a, int64_t planes, int64_t nfields) {
+  return dim3((unsigned)((a.ncols + a.C - 1) / a.C), (unsigned)planes, (unsigned)nfields);
+}
+dim3 row_grid(const RowArgs& r) { return dim3((unsigned)((r.nrows + r.C - 1) / r.C)); }
+
+#define LAUNCH(call, where)                                   \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where);      \
+  } while (0)
+
+// A launch bracketed by timing events when the plan records them.
+#define TLAUNCH(kind, call, where)                                                   \
+  do {                                                                               \
+    const bool t_ = p->tused < p->tcap;                                              \
+    if (t_) cudaEventRecord(p->tev[2 * p->tused], s);                                \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where);                              \
+    if (t_) {                                                                        \
+      cudaEventRecord(p->tev[2 * p->tused + 1], s);                                  \
+      p->tkind[p->tused] = (kind);                                                   \
+    }                                                                                \
+    if (p->tcap > 0) ++p->tused;                                                     \
+  } while (0)
+
+// FP32 sampling of fields [f0, f0 + nb) into out (already offset to field f0).
+grf_status sample_chunk_fp32(grf_plan p, uint64_t seed, int64_t f0, int64_t nb, float* out, cudaStream_t s) {
+  const HalfGeom g = half_geom(p, seed, f0);
+  if (p->d == 1) {
+    RowArgs r = row_args(p, g, nb, 1);
+    r.outR = out;
+    if (p->alg == 2) TLAUNCH(GRF_KERNEL_ROWS_1D, launch_row(ROW_NOISE_H, ROW_C2R, p->row.P, r, row_grid(r), s), "1-D c2r");
+    else TLAUNCH(GRF_KERNEL_ROWS_1D, launch_row(ROW_NOISE_REAL, ROW_R2C_SCALE_C2R, p->row.P, r, row_grid(r), s), "1-D alg1");
+    return GRF_OK;
+  }
+  const int T = p->d == 2 ? p->T : 1;
+  if (p->alg == 2) {
+    ColArgs a = col_axis1(p, g, nullptr, p->ws, T);
+    TLAUNCH(GRF_KERNEL_NOISE_COLUMNS, launch_col(COL_NOISE, COL_INV, p->colA.P, a, col_grid(a, 1, nb), s), "noise + axis-1 pass");
+  } else {
+    RowArgs r = row_args(p, g, nb, T);
+    r.outH = p->ws;
+    TLAUNCH(GRF_KERNEL_ROWS_R2C, launch_row(ROW_NOISE_REAL, ROW_R2C, p->row.P, r, row_grid(r), s), "alg1 noise + r2c");
+    if (p->d == 3) {
+      ColArgs b = col_axis2(p, g, p->ws, p->ws);
+      TLAUNCH(GRF_KERNEL_COLUMNS, launch_col(COL_LOAD, COL_FWD, p->colB.P, b, col_grid(b, p->N1, nb), s), "alg1 axis-2 forward");
+    }
+    ColArgs a = col_axis1(p, g, p->ws, p->ws, T);
+    TLAUNCH(GRF_KERNEL_COLUMNS, launch_col(COL_LOAD, COL_FWD_SCALE_INV, p->colA.P, a, col_grid(a, 1, nb), s), "alg1 axis-1 scale");
+  }
+  if (p->d == 3) {
+    ColArgs b = col_axis2(p, g, p->ws, p->ws);
+    TLAUNCH(GRF_KERNEL_COLUMNS, launch_col(COL_LOAD, COL_INV, p->colB.P, b, col_grid(b, p->N1, nb), s), "axis-2 inverse");
+  }
+  RowArgs r = row_args(p, g, nb, T);
+  r.inH = p->ws;
+  r.outR = out;
+  TLAUNCH(GRF_KERNEL_ROWS_C2R, launch_row(ROW_LOAD_H, ROW_C2R, p->row.P, r, row_grid(r), s), "c2r pass");
+  return GRF_OK;
+}
+
+grf_status check_plan(grf_plan p) {
+  if (!p) return fail(GRF_ERR_INVALID_ARG, "plan is NULL");
+  return GRF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* grf_status_string(grf_status s) {
+  switch (s) {
+    case GRF_OK: return "ok";
+    case GRF_ERR_INVALID_ARG: return "invalid argument";
+    case GRF_ERR_UNSUPPORTED: return "unsupported configuration";
+    case GRF_ERR_OOM: return "out of device memory";
+    case GRF_ERR_CUDA: return "CUDA error";
+    case GRF_ERR_TIMEOUT: return "device wait timed out";
+    case GRF_ERR_NOT_HERMITIAN: return "input is not Hermitian";
+    default: return "unknown status";
+  }
+}
+
+const char* grf_last_error(void) { return g_last_error.c_str(); }
+
+grf_status grf_plan_create(grf_plan* out, int d, const int64_t* n, const double* L, const grf_spectrum* spec,
+                           int alg, int prec, int64_t max_batch) {
+  g_last_error.clear();
+  if (!out) return fail(GRF_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (d < 1 || d > 3) return fail(GRF_ERR_INVALID_ARG, "d must be 1, 2 or 3");
+  if (!n || !L) return fail(GRF_ERR_INVALID_ARG, "n or L is NULL");
+  grf_status st = validate_spec(spec);
+  if (st != GRF_OK) return st;
+  if (alg != GRF_ALG_ONE_FFT && alg != GRF_ALG_TWO_FFT) return fail(GRF_ERR_INVALID_ARG, "alg must be 1 or 2");
+  if (prec != GRF_FP32 && prec != GRF_FP64) return fail(GRF_ERR_INVALID_ARG, "prec must be 0 or 1");
+  if (max_batch < 1 || max_batch > 65535) return fail(GRF_ERR_INVALID_ARG, "max_batch must be in [1, 65535]");
+  for (int i = 0; i < d; ++i) {
+    if (n[i] < 2 || (n[i] & 1)) return fail(GRF_ERR_INVALID_ARG, "every N_i must be even and >= 2");
+    if (!(L[i] > 0) || !std::isfinite(L[i])) return fail(GRF_ERR_INVALID_ARG, "every L_i must be > 0");
+  }
+  for (int i = 0; i < d; ++i) {
+    if (!is_pow2(n[i])) return fail(GRF_ERR_UNSUPPORTED, "N_i must be a power of two");
+    const int64_t lim = (i < d - 1) ? 4096 : 8192;
+    if (n[i] > lim) return fail(GRF_ERR_UNSUPPORTED, "grid size above the supported maximum");
+  }
+
+  grf_plan p = new (std::nothrow) grf_plan_s();
+  if (!p) return fail(GRF_ERR_OOM, "host allocation");
+  p->d = d;
+  for (int i = 0; i < d; ++i) {
+    p->n[i] = n[i];
+    p->L[i] = L[i];
+  }
+  p->spec = *spec;
+  p->alg = alg;
+  p->prec = prec;
+  p->max_batch = max_batch;
+  cudaGetDevice(&p->device);
+  p->M = (int)(n[d - 1] / 2);
+  p->N1 = d >= 2 ? (int)n[0] : 1;
+  p->Nmid = d == 3 ? (int)n[1] : 1;
+  p->ntot = 1;
+  for (int i = 0; i < d; ++i) p->ntot *= n[i];
+  p->hsize = (int64_t)p->N1 * p->Nmid * (p->M + 1);
+  p->fold_size = (int64_t)(p->N1 / 2 + 1) * (p->Nmid / 2 + 1) * (p->M + 1);
+  if (spec->normalize_discrete) {
+    const double tot = discrete_sum(p);
+    p->norm_scale = spec->sigma * spec->sigma / tot;
+  }
+
+  int64_t maxlen = 2;
+  for (int i = 0; i < d; ++i) maxlen = maxlen > n[i] ? maxlen : n[i];
+  p->twmax = (int)maxlen;
+  cudaStream_t s = nullptr;
+  const SpecParams sp = spec_params(p);
+  cudaError_t e;
+#define PLAN_CUDA(call, where)                 \
+  do {                                         \
+    e = (call);                                \
+    if (e != cudaSuccess) {                    \
+      grf_status r_ = cuda_fail(e, where);     \
+      free_plan(p);                            \
+      return r_;                               \
+    }                                          \
+  } while (0)
+
+  PLAN_CUDA(dmalloc(&p->status, 1), "status word");
+  PLAN_CUDA(cudaMemset(p->status, 0, sizeof(int)), "status word");
+  if (prec == GRF_FP32) {
+    PLAN_CUDA(dmalloc(&p->tw, 2 * maxlen), "twiddle table");
+    PLAN_CUDA(build_twiddles(p->tw, (int)maxlen, s), "twiddle build");
+    PLAN_CUDA(dmalloc(&p->stab, p->fold_size), "s table");
+    const bool grad = spec->family <= 1 && !spec->normalize_discrete;
+    double dig = 0.0;
+    if (grad) {
+      PLAN_CUDA(dmalloc(&p->dstab, 2 * p->fold_size), "ds table");
+      if (spec->family == 0) dig = digamma_host(spec->nu + 0.5 * d) - digamma_host(spec->nu);
+    }
+    PLAN_CUDA(build_stab(p->stab, p->dstab, sp, dig, s), "s table build");
+    // schedules
+    if (d == 1) {
+      p->row = choose_row(p->M, max_batch);
+    } else {
+      p->colA = choose_col(p->N1, (int64_t)p->Nmid * (p->M + 1));
+      if (d == 3) p->colB = choose_col(p->Nmid, p->M + 1);
+      p->row = choose_row(p->M, max_batch * (p->ntot / n[d - 1]));
+      p->T = 1;
+      if (d == 2 && p->N1 >= 256) {
+        p->T = 8;
+        while (p->T > 1 && p->N1 % p->T) p->T >>= 1;
+      }
+      p->chunk = max_batch;
+      PLAN_CUDA(dmalloc(&p->ws, (size_t)(p->chunk * p->hsize)), "workspace");
+    }
+  } else {
+    PLAN_CUDA(dmalloc(&p->tw64, 2 * maxlen), "FP64 twiddle table");
+    PLAN_CUDA(build_twiddles_d(p->tw64, (int)maxlen, s), "FP64 twiddle build");
+    PLAN_CUDA(dmalloc(&p->stab64, p->fold_size), "FP64 s table");
+    PLAN_CUDA(build_stab_d(p->stab64, sp, s), "FP64 s table build");
+    PLAN_CUDA(dmalloc(&p->bufA, p->ntot), "FP64 buffer");
+    PLAN_CUDA(dmalloc(&p->bufB, p->ntot), "FP64 buffer");
+  }
+  PLAN_CUDA(cudaStreamSynchronize(s), "plan table build");
+#undef PLAN_CUDA
+  *out = p;
+  return GRF_OK;
+}
+
+grf_status grf_plan_set_spectrum(grf_plan p, const grf_spectrum* spec, void* stream) {
+  grf_status st = check_plan(p);
+  if (st != GRF_OK) return st;
+  if (p->kind != 0) return fail(GRF_ERR_INVALID_ARG, "batch plans keep their spectra");
+  st = validate_spec(spec);
+  if (st != GRF_OK) return st;
+  if (spec->family != p->spec.family || (spec->normalize_discrete != 0) != (p->spec.normalize_discrete != 0))
+    return fail(GRF_ERR_INVALID_ARG, "the family and normalisation mode are fixed at plan creation");
+  cudaStream_t s = (cudaStream_t)stream;
+  p->spec = *spec;
+  p->norm_scale = spec->normalize_discrete ? spec->sigma * spec->sigma / discrete_sum(p) : 1.0;
+  const SpecParams sp = spec_params(p);
+  if (p->prec == GRF_FP32) {
+    double dig = 0.0;
+    if (spec->family == 0) dig = digamma_host(spec->nu + 0.5 * p->d) - digamma_host(spec->nu);
+    LAUNCH(build_stab(p->stab, p->dstab, sp, dig, s), "s table build");
+  } else {
+    LAUNCH(build_stab_d(p->stab64, sp, s), "FP64 s table build");
+  }
+  return GRF_OK;
+}
+
+grf_status grf_sample(grf_plan p, uint64_t seed, int64_t batch, void* out, void* stream) {
+  grf_status st = check_plan(p);
+  if (st != GRF_OK) return st;
+  if (p->kind != 0) return fail(GRF_ERR_INVALID_ARG, "batch plans use grf_batch_sample");
+  if (!out) return fail(GRF_ERR_INVALID_ARG, "out is NULL");
+  if (batch < 1 || batch > p->max_batch) return fail(GRF_ERR_INVALID_ARG, "batch must be in [1, max_batch]");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (p->prec == GRF_FP64) {
+    Plain64Geom g{};
+    g.d = p->d;
+    for (int i = 0; i < 3; ++i) g.n[i] = (int)p->n[i];
+    for (int64_t b = 0; b < batch; ++b) {
+      TLAUNCH(GRF_KERNEL_PLAIN64,
+              plain64_field(g, p->alg, seed + (uint64_t)b, p->stab64, p->tw64, p->bufA, p->bufB,
+                            (double*)out + b * p->ntot, s),
+              "FP64 plain field");
+    }
+    return GRF_OK;
+  }
+  const int64_t chunk = p->d == 1 ? batch : p->chunk;
+  for (int64_t f0 = 0; f0 < batch; f0 += chunk) {
+    const int64_t nb = batch - f0 < chunk ? batch - f0 : chunk;
+    st = sample_chunk_fp32(p, seed, f0, nb, (float*)out + f0 * p->ntot, s);
+    if (st != GRF_OK) return st;
+  }
+  return GRF_OK;
+}
+
+grf_status grf_sample_host(grf_plan p, uint64_t seed, int64_t batch, void* host_out, void* stream) {
+  grf_status st = check_plan(p);
+  if (st != GRF_OK) return st;
+  if (p->kind != 0) return fail(GRF_ERR_INVALID_ARG, "batch plans use grf_batch_sample");
+  if (!host_out) return fail(GRF_ERR_INVALID_ARG, "host_out is NULL");
+  if (batch < 1 || batch > p->max_batch) return fail(GRF_ERR_INVALID_ARG, "batch must be in [1, max_batch]");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t esz = p->prec == GRF_FP64 ? sizeof(double) : sizeof(float);
+  const size_t field_bytes = (size_t)p->ntot * esz;
+  int64_t per = (int64_t)((64u << 20) / field_bytes);
+  if (per < 1) per = 1;
+  if (p->prec == GRF_FP32 && p->d > 1 && per > p->chunk) per = p->chunk;
+  if (per > batch) per = batch;
+  if (p->stage_fields < per) {
+    for (int i = 0; i < 2; ++i) {
+      cudaFree(p->stage[i]);
+      p->stage[i] = nullptr;
+    }
+    p->stage_fields = 0;
+    for (int i = 0; i < 2; ++i) GRF_CUDA(cudaMalloc(&p->stage[i], per * field_bytes), "host staging buffer");
+    p->stage_fields = per;
+  }
+  if (!p->copy_stream) {
+    GRF_CUDA(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking), "copy stream");
+    for (int i = 0; i < 2; ++i) {
+      GRF_CUDA(cudaEventCreateWithFlags(&p->ev_done[i], cudaEventDisableTiming), "event");
+      GRF_CUDA(cudaEventCreateWithFlags(&p->ev_copied[i], cudaEventDisableTiming), "event");
+    }
+  }
+  int64_t idx = 0;
+  for (int64_t f0 = 0; f0 < batch; f0 += per, ++idx) {
+    const int64_t nb = batch - f0 < per ? batch - f0 : per;
+    const int slot = (int)(idx & 1);
+    if (idx >= 2) GRF_CUDA(cudaStreamWaitEvent(s, p->ev_copied[slot], 0), "wait copy");
+    if (p->prec == GRF_FP64) {
+      Plain64Geom g{};
+      g.d = p->d;
+      for (int i = 0; i < 3; ++i) g.n[i] = (int)p->n[i];
+      for (int64_t b = 0; b < nb; ++b)
+        LAUNCH(plain64_field(g, p->alg, seed + (uint64_t)(f0 + b), p->stab64, p->tw64, p->bufA, p->bufB,
+                             (double*)p->stage[slot] + b * p->ntot, s),
+               "FP64 plain field");
+    } else {
+      st = sample_chunk_fp32(p, seed, f0, nb, (float*)p->stage[slot], s);
+      if (st != GRF_OK) return st;
+    }
+    GRF_CUDA(cudaEventRecord(p->ev_done[slot], s), "record");
+    GRF_CUDA(cudaStreamWaitEvent(p->copy_stream, p->ev_done[slot], 0), "wait compute");
+    GRF_CUDA(cudaMemcpyAsync((char*)host_out + (size_t)f0 * field_bytes, p->stage[slot], nb * field_bytes,
+                             cudaMemcpyDeviceToHost, p->copy_stream),
+             "copy to host");
+    GRF_CUDA(cudaEventRecord(p->ev_copied[slot], p->copy_stream), "record");
+  }
+  GRF_CUDA(cudaStreamSynchronize(p->copy_stream), "copy sync");
+  return GRF_OK;
+}
+
+grf_status grf_backward(grf_plan p, uint64_t seed, int64_t batch, const void* grad_out, double* grad_params,
+                        void* stream) {
+  grf_status st = check_plan(p);
+  if (st != GRF_OK) return st;
+  if (p->kind != 0) return fail(GRF_ERR_INVALID_ARG, "batch plans have no adjoint");
+  if (!grad_out || !grad_params) return fail(GRF_ERR_INVALID_ARG, "NULL pointer");
+  if (batch < 1 || batch > p->max_batch) return fail(GRF_ERR_INVALID_ARG, "batch must be in [1, max_batch]");
+  if (p->prec != GRF_FP32 || p->alg != GRF_ALG_ONE_FFT)
+    return fail(GRF_ERR_UNSUPPORTED, "the adjoint is built for FP32 Algorithm 2 plans");
+  if (!p->dstab) return fail(GRF_ERR_UNSUPPORTED, "the adjoint needs a Matern or Gaussian spectrum without normalize_discrete");
+  cudaStream_t s = (cudaStream_t)stream;
+  const float* G = (const float*)grad_out;
+  if (p->d == 1) {
+    const HalfGeom g = half_geom(p, seed, 0);
+    RowArgs r = row_args(p, g, batch, 1);
+    r.inR = G;
+    r.partial = grad_params;
+    TLAUNCH(GRF_KERNEL_ROWS_1D, launch_row(ROW_LOAD_REAL, ROW_R2C_ADJ, p->row.P, r, row_grid(r), s), "1-D adjoint");
+    return GRF_OK;
+  }
+  const int T = p->d == 2 ? p->T : 1;
+  for (int64_t f0 = 0; f0 < batch; f0 += p->chunk) {
+    const int64_t nb = batch - f0 < p->chunk ? batch - f0 : p->chunk;
+    const HalfGeom g = half_geom(p, seed, f0);
+    RowArgs r = row_args(p, g, nb, T);
+    r.inR = G + f0 * p->ntot;
+    r.outH = p->ws;
+    TLAUNCH(GRF_KERNEL_ROWS_R2C, launch_row(ROW_LOAD_REAL, ROW_R2C, p->row.P, r, row_grid(r), s), "adjoint r2c");
+    if (p->d == 3) {
+      ColArgs b = col_axis2(p, g, p->ws, p->ws);
+      TLAUNCH(GRF_KERNEL_COLUMNS, launch_col(COL_LOAD, COL_FWD, p->colB.P, b, col_grid(b, p->N1, nb), s), "adjoint axis 2");
+    }
+    ColArgs a = col_axis1(p, g, p->ws, nullptr, T);
+    const dim3 grid = col_grid(a, 1, nb);
+    const int64_t nblk = (int64_t)grid.x;
+    st = ensure_partial(p, nblk * nb);
+    if (st != GRF_OK) return st;
+    a.partial = p->partial;
+    TLAUNCH(GRF_KERNEL_COLUMNS, launch_col(COL_LOAD, COL_FWD_ADJ, p->colA.P, a, grid, s), "adjoint reduction");
+    TLAUNCH(GRF_KERNEL_REDUCE, reduce_partials(p->partial, nblk, nb, grad_params + 3 * f0, s), "adjoint final sum");
+  }
+  return GRF_OK;
+}
+
+grf_status grf_rfft_forward(grf_plan p, int64_t batch, const void* in, void* out_halfspec, void* stream) {
+  grf_status st = check_plan(p);
+  if (st != GRF_OK) return st;
+  if (p->kind != 0) return fail(GRF_ERR_INVALID_ARG, "batch plans have no rfft");
+  if (!in || !out_halfspec) return fail(GRF_ERR_INVALID_ARG, "NULL pointer");
+  if (batch < 1 || batch > p->max_batch) return fail(GRF_ERR_INVALID_ARG, "batch must be in [1, max_batch]");
+  if (p->prec != GRF_FP32) return fail(GRF_ERR_UNSUPPORTED, "rfft is built for FP32 plans");
+  cudaStream_t s = (cudaStream_t)stream;
+  const HalfGeom g = half_geom(p, 0, 0);
+  float2* H = (float2*)out_halfspec;
+  RowArgs r = row_args(p, g, batch, 1);
+  r.inR = (const float*)in;
+  r.outH = H;
+  TLAUNCH(GRF_KERNEL_ROWS_R2C, launch_row(ROW_LOAD_REAL, ROW_R2C, p->row.P, r, row_grid(r), s), "rfft rows");
+  if (p->d == 3) {
+    ColArgs b = col_axis2(p, g, H, H);
+    TLAUNCH(GRF_KERNEL_COLUMNS, launch_col(COL_LOAD, COL_FWD, p->colB.P, b, col_grid(b, p->N1, batch), s), "rfft axis 2");
+  }
+  if (p->d >= 2) {
+    ColArgs a = col_axis1(p, g, H, H, 1);
+    TLAUNCH(GRF_KERNEL_COLUMNS, launch_col(COL_LOAD, COL_FWD, p->colA.P, a, col_grid(a, 1, batch), s), "rfft axis 1");
+  }
+  return GRF_OK;
+}
+
+grf_status grf_batch_plan_create(grf_plan* out, int64_t count, const int* d, const int64_t* n, const double* L,
+                                 const grf_spectrum* spec, int prec) {
+  g_last_error.clear();
+  if (!out) return fail(GRF_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (count < 1 || !d || !n || !L || !spec) return fail(GRF_ERR_INVALID_ARG, "bad batch description");
+  if (prec != GRF_FP32) return fail(GRF_ERR_UNSUPPORTED, "batch plans are FP32");
+  for (int64_t i = 0; i < count; ++i) {
+    grf_status st = validate_spec(spec + i);
+    if (st != GRF_OK) return st;
+    if (spec[i].family > 1) return fail(GRF_ERR_UNSUPPORTED, "batch plans take Matern or Gaussian spectra");
+  }
+  grf_plan p = new (std::nothrow) grf_plan_s();
+  if (!p) return fail(GRF_ERR_OOM, "host allocation");
+  p->kind = 1;
+  std::string err;
+  grf_status st = batch_plan_build(&p->batch, count, d, n, L, spec, &err);
+  if (st != GRF_OK) {
+    free_plan(p);
+    return fail(st, err);
+  }
+  cudaError_t e = dmalloc(&p->status, 1);
+  if (e == cudaSuccess) e = cudaMemset(p->status, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    free_plan(p);
+    return cuda_fail(e, "status word");
+  }
+  *out = p;
+  return GRF_OK;
+}
+
+grf_status grf_batch_sample(grf_plan p, uint64_t seed, void* const* out, void* stream) {
+  grf_status st = check_plan(p);
+  if (st != GRF_OK) return st;
+  if (p->kind != 1) return fail(GRF_ERR_INVALID_ARG, "not a batch plan");
+  if (!out) return fail(GRF_ERR_INVALID_ARG, "out is NULL");
+  std::string err;
+  st = batch_plan_sample(p->batch, seed, out, (cudaStream_t)stream, p->status, false, &err);
+  return st == GRF_OK ? st : fail(st, err);
+}
+
+grf_status grf_batch_graph_launch(grf_plan p, uint64_t seed, void* const* out, void* stream) {
+  grf_status st = check_plan(p);
+  if (st != GRF_OK) return st;
+  if (p->kind != 1) return fail(GRF_ERR_INVALID_ARG, "not a batch plan");
+  if (!out) return fail(GRF_ERR_INVALID_ARG, "out is NULL");
+  std::string err;
+  st = batch_plan_sample(p->batch, seed, out, (cudaStream_t)stream, p->status, true, &err);
+  return st == GRF_OK ? st : fail(st, err);
+}
+
+grf_status grf_status_word(grf_plan p, void* stream) {
+  grf_status st = check_plan(p);
+  if (st != GRF_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  GRF_CUDA(cudaStreamSynchronize(s), "status sync");
+  int h = 0;
+  GRF_CUDA(cudaMemcpy(&h, p->status, sizeof(int), cudaMemcpyDeviceToHost), "status read");
+  GRF_CUDA(cudaMemset(p->status, 0, sizeof(int)), "status clear");
+  return (grf_status)h;
+}
+
+grf_status grf_philox_words(uint64_t key, uint32_t tag, uint64_t q0, int64_t count, uint32_t* out_words,
+                            void* stream) {
+  if (!out_words || count < 0) return fail(GRF_ERR_INVALID_ARG, "bad philox_words arguments");
+  if (count == 0) return GRF_OK;
+  LAUNCH(philox_words(key, tag, q0, count, out_words, (cudaStream_t)stream), "philox words");
+  return GRF_OK;
+}
+
+grf_status grf_plan_timing(grf_plan p, int64_t cap) {
+  grf_status st = check_plan(p);
+  if (st != GRF_OK) return st;
+  if (cap < 0) return fail(GRF_ERR_INVALID_ARG, "cap must be >= 0");
+  for (cudaEvent_t e : p->tev) cudaEventDestroy(e);
+  p->tev.clear();
+  p->tkind.assign((size_t)cap, -1);
+  p->tev.resize((size_t)(2 * cap), nullptr);
+  for (auto& e : p->tev) GRF_CUDA(cudaEventCreate(&e), "timing event");
+  p->tcap = cap;
+  p->tused = 0;
+  return GRF_OK;
+}
+
+int64_t grf_plan_timing_read(grf_plan p, int* kinds, float* ms, int64_t cap_out) {
+  if (!p) return -1;
+  const int64_t n = p->tused;
+  const int64_t rec = n < p->tcap ? n : p->tcap;
+  for (int64_t i = 0; i < rec && i < cap_out; ++i) {
+    float t = 0.f;
+    if (cudaEventSynchronize(p->tev[2 * i + 1]) != cudaSuccess ||
+        cudaEventElapsedTime(&t, p->tev[2 * i], p->tev[2 * i + 1]) != cudaSuccess)
+      t = -1.f;
+    if (kinds) kinds[i] = p->tkind[i];
+    if (ms) ms[i] = t;
+  }
+  p->tused = 0;
+  return n;
+}
+
+int64_t grf_plan_query(grf_plan p, int key) {
+  if (!p) return -1;
+  if (p->kind == 1) {
+    if (key == 0) return batch_plan_total_points(p->batch);
+    return -1;
+  }
+  switch (key) {
+    case 0: return p->ntot;
+    case 1: return p->hsize;
+    case 2: return (int64_t)(p->chunk * p->hsize * (int64_t)sizeof(float2));
+    case 3: return p->d;
+    case 4: return p->n[0];
+    case 5: return p->n[1];
+    case 6: return p->n[2];
+    default: return -1;
+  }
+}
+
+grf_status grf_plan_destroy(grf_plan p) {
+  if (!p) return GRF_OK;
+  cudaSetDevice(p->device);
+  free_plan(p);
+  return GRF_OK;
+}
+
+}  // extern "C"

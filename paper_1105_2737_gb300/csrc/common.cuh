@@ -1,0 +1,159 @@
+// Device helpers shared by the GRF kernels: complex arithmetic, the
+// Philox4x32-10 counter-based generator and the Box-Muller transform.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define GRF_DEV __device__ __forceinline__
+
+namespace grf {
+
+GRF_DEV float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+GRF_DEV float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+GRF_DEV float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+GRF_DEV float2 cmulc(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+GRF_DEV float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+GRF_DEV float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+GRF_DEV double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+GRF_DEV double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+GRF_DEV double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+GRF_DEV double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+GRF_DEV double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of
+//   (hi0, lo0) = M0 * c0, (hi1, lo1) = M1 * c2,
+//   c <- (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0),
+// with the key bumped by the Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+struct u32x4 {
+  uint32_t x, y, z, w;
+};
+
+GRF_DEV u32x4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                            uint32_t k1) {
+  constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  constexpr uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += W0;
+      k1 += W1;
+    }
+    const uint32_t lo0 = M0 * c0, hi0 = __umulhi(M0, c0);
+    const uint32_t lo1 = M1 * c2, hi1 = __umulhi(M1, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ k0;
+    const uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  return u32x4{c0, c1, c2, c3};
+}
+
+// Call q (64-bit) with counter (q_lo, q_hi, tag, 0) and key (lo, hi) of `key`.
+GRF_DEV u32x4 philox_call(uint64_t q, uint32_t tag, uint64_t key) {
+  return philox4x32_10((uint32_t)q, (uint32_t)(q >> 32), tag, 0u, (uint32_t)key,
+                       (uint32_t)(key >> 32));
+}
+
+// u = (2 (x >> 9) + 1) 2^-24: exact in FP32, in (0, 1).
+GRF_DEV float uniform_open(uint32_t x) {
+  return (float)((x >> 9) * 2u + 1u) * 5.9604644775390625e-8f;
+}
+GRF_DEV double uniform_open_d(uint32_t x) {
+  return (double)((x >> 9) * 2u + 1u) * 5.9604644775390625e-8;
+}
+
+// Box-Muller: rho = sqrt(-2 ln u_a), (z_re, z_im) = rho (cos 2 pi u_b, sin 2 pi u_b).
+// CUDA's accurate logf and sincospif are called (2 u_b is exact in FP32).
+GRF_DEV float2 box_muller(uint32_t wa, uint32_t wb) {
+  const float ua = uniform_open(wa);
+  const float ub = uniform_open(wb);
+  const float rho = sqrtf(-2.0f * logf(ua));
+  float s, c;
+  sincospif(2.0f * ub, &s, &c);
+  return make_float2(rho * c, rho * s);
+}
+GRF_DEV double2 box_muller_d(uint32_t wa, uint32_t wb) {
+  const double ua = uniform_open_d(wa);
+  const double ub = uniform_open_d(wb);
+  const double rho = sqrt(-2.0 * log(ua));
+  double s, c;
+  sincospi(2.0 * ub, &s, &c);
+  return make_double2(rho * c, rho * s);
+}
+
+// The normal pair of Algorithm 2 for half-spectrum entry (row r, last index kd):
+// call r * Q + (kd >> 1), words 2 (kd & 1) and 2 (kd & 1) + 1.
+GRF_DEV float2 alg2_normals(uint64_t row, int kd, uint32_t Q, uint64_t key) {
+  const u32x4 w = philox_call(row * (uint64_t)Q + (uint64_t)(kd >> 1), 0u, key);
+  return (kd & 1) ? box_muller(w.z, w.w) : box_muller(w.x, w.y);
+}
+GRF_DEV double2 alg2_normals_d(uint64_t row, int kd, uint32_t Q, uint64_t key) {
+  const u32x4 w = philox_call(row * (uint64_t)Q + (uint64_t)(kd >> 1), 0u, key);
+  return (kd & 1) ? box_muller_d(w.z, w.w) : box_muller_d(w.x, w.y);
+}
+
+// Hermitian noise xi_K of Algorithm 2 at a half-spectrum entry.
+//   row  : row-major index over (k_1 .. k_{d-1}) of K
+//   nrow : the same index of -K (mod N) (only read on the planes kd in {0, M})
+//   kd   : last index, 0..M
+// Off the planes: (z_re + i z_im)/sqrt 2.  On the planes: the member of {K, -K}
+// with the larger index keeps its own normals, the other takes the conjugate;
+// a self-conjugate K (row == nrow) takes the real normal z_re.
+GRF_DEV float2 alg2_xi(uint64_t row, uint64_t nrow, int kd, int M, uint32_t Q, uint64_t key) {
+  const float r2 = 0.70710678118654752440f;
+  if (kd != 0 && kd != M) {
+    const float2 z = alg2_normals(row, kd, Q, key);
+    return make_float2(z.x * r2, z.y * r2);
+  }
+  if (row == nrow) {
+    const float2 z = alg2_normals(row, kd, Q, key);
+    return make_float2(z.x, 0.0f);
+  }
+  if (row > nrow) {
+    const float2 z = alg2_normals(row, kd, Q, key);
+    return make_float2(z.x * r2, z.y * r2);
+  }
+  const float2 z = alg2_normals(nrow, kd, Q, key);
+  return make_float2(z.x * r2, -z.y * r2);
+}
+GRF_DEV double2 alg2_xi_d(uint64_t row, uint64_t nrow, int kd, int M, uint32_t Q, uint64_t key) {
+  const double r2 = 0.70710678118654752440;
+  const uint64_t src = (kd != 0 && kd != M) ? row : (row >= nrow ? row : nrow);
+  const double2 z = alg2_normals_d(src, kd, Q, key);
+  if (kd != 0 && kd != M) return make_double2(z.x * r2, z.y * r2);
+  if (row == nrow) return make_double2(z.x, 0.0);
+  if (row > nrow) return make_double2(z.x * r2, z.y * r2);
+  return make_double2(z.x * r2, -z.y * r2);
+}
+
+// Real normal of Algorithm 1 at flat grid index j: call j >> 2, pair t = (j & 3) >> 1,
+// even j the cosine normal, odd j the sine normal.
+GRF_DEV float alg1_normal(uint64_t j, uint64_t key) {
+  const u32x4 w = philox_call(j >> 2, 1u, key);
+  const float2 z = ((j & 3) >> 1) ? box_muller(w.z, w.w) : box_muller(w.x, w.y);
+  return (j & 1) ? z.y : z.x;
+}
+// Both reals of the pair (j even, j + 1) in one call.
+GRF_DEV float2 alg1_normal_pair(uint64_t j_even, uint64_t key) {
+  const u32x4 w = philox_call(j_even >> 2, 1u, key);
+  return ((j_even & 3) >> 1) ? box_muller(w.z, w.w) : box_muller(w.x, w.y);
+}
+GRF_DEV double alg1_normal_d(uint64_t j, uint64_t key) {
+  const u32x4 w = philox_call(j >> 2, 1u, key);
+  const double2 z = ((j & 3) >> 1) ? box_muller_d(w.z, w.w) : box_muller_d(w.x, w.y);
+  return (j & 1) ? z.y : z.x;
+}
+
+}  // namespace grf

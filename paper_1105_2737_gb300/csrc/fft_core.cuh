@@ -1,0 +1,186 @@
+// CTA-level Stockham FFT engine (FP32 data, twiddles from FP64-built tables).
+//
+// A CTA transforms C independent sequences of length N = TPT * P at once; each
+// thread owns P points of one sequence in registers.  Thread (c, tau) holds
+// the points at positions tau + TPT * q, q = 0..P-1, both on entry (input
+// order) and on exit (output order): the Stockham autosort formulation
+// (stage with radix R and span Ns: butterfly j reads j + r N/R and writes
+// (j / Ns) Ns R + j % Ns + r Ns) leaves the first stage's read set and the
+// last stage's write set on the same registers.  Stages are radix 16 (an
+// in-register DIF network) with one final radix 2/4/8 stage if log2 N is not
+// a multiple of 4; between stages the points go through shared memory, in an
+// interleaved layout (c fastest) padded by one element every 16 positions so
+// that the stage writes of a half warp hit distinct banks.
+#pragma once
+#include <type_traits>
+#include "common.cuh"
+
+namespace grf {
+
+template <int I, int E, class F>
+GRF_DEV void static_for(F&& f) {
+  if constexpr (I < E) {
+    f(std::integral_constant<int, I>{});
+    static_for<I + 1, E>(f);
+  }
+}
+
+__host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x / 2); }
+__host__ __device__ constexpr int bitrevc(int x, int bits) {
+  int r = 0;
+  for (int i = 0; i < bits; ++i) r = (r << 1) | ((x >> i) & 1);
+  return r;
+}
+
+// cos and sin of 2 pi e / 16.
+constexpr double kC16[16] = {1.0,
+                             0.92387953251128675613,
+                             0.70710678118654752440,
+                             0.38268343236508977173,
+                             0.0,
+                             -0.38268343236508977173,
+                             -0.70710678118654752440,
+                             -0.92387953251128675613,
+                             -1.0,
+                             -0.92387953251128675613,
+                             -0.70710678118654752440,
+                             -0.38268343236508977173,
+                             0.0,
+                             0.38268343236508977173,
+                             0.70710678118654752440,
+                             0.92387953251128675613};
+constexpr double kS16[16] = {0.0,
+                             0.38268343236508977173,
+                             0.70710678118654752440,
+                             0.92387953251128675613,
+                             1.0,
+                             0.92387953251128675613,
+                             0.70710678118654752440,
+                             0.38268343236508977173,
+                             0.0,
+                             -0.38268343236508977173,
+                             -0.70710678118654752440,
+                             -0.92387953251128675613,
+                             -1.0,
+                             -0.92387953251128675613,
+                             -0.70710678118654752440,
+                             -0.38268343236508977173};
+
+// a * exp(DIR 2 pi i E / R), R <= 16, with the trivial factors written out.
+template <int E, int R, int DIR>
+GRF_DEV float2 twmul(float2 a) {
+  constexpr int e = ((E * (16 / R)) % 16 + 16) % 16;
+  if constexpr (e == 0) {
+    return a;
+  } else if constexpr (e == 8) {
+    return make_float2(-a.x, -a.y);
+  } else if constexpr (e == 4) {
+    if constexpr (DIR > 0) return make_float2(-a.y, a.x);
+    else return make_float2(a.y, -a.x);
+  } else if constexpr (e == 12) {
+    if constexpr (DIR > 0) return make_float2(a.y, -a.x);
+    else return make_float2(-a.y, a.x);
+  } else {
+    constexpr float c = (float)kC16[e];
+    constexpr float s = DIR > 0 ? (float)kS16[e] : -(float)kS16[e];
+    return make_float2(fmaf(c, a.x, -s * a.y), fmaf(c, a.y, s * a.x));
+  }
+}
+
+// In-register DFT of R points (R a power of two <= 16):
+// X[k] = sum_n x[n] exp(DIR 2 pi i n k / R).  x[STRIDE * i + OFF] holds point i.
+template <int R, int DIR, int STRIDE, int OFF, int NV>
+GRF_DEV void dft_regs(float2 (&x)[NV]) {
+  if constexpr (R == 1) {
+    return;
+  } else {
+    constexpr int LG = ilog2c(R);
+    static_for<0, LG>([&](auto lv) {
+      constexpr int span = R >> (decltype(lv)::value + 1);
+      static_for<0, R / (2 * span)>([&](auto blk) {
+        static_for<0, span>([&](auto k) {
+          constexpr int i0 = decltype(blk)::value * 2 * span + decltype(k)::value;
+          constexpr int i1 = i0 + span;
+          const float2 a = x[STRIDE * i0 + OFF], b = x[STRIDE * i1 + OFF];
+          x[STRIDE * i0 + OFF] = cadd(a, b);
+          x[STRIDE * i1 + OFF] = twmul<decltype(k)::value*(R / (2 * span)), R, DIR>(csub(a, b));
+        });
+      });
+    });
+    float2 y[R];
+    static_for<0, R>([&](auto k) { y[decltype(k)::value] = x[STRIDE * bitrevc(decltype(k)::value, LG) + OFF]; });
+    static_for<0, R>([&](auto k) { x[STRIDE * decltype(k)::value + OFF] = y[decltype(k)::value]; });
+  }
+}
+
+// Padded shared-memory position.
+GRF_DEV int spad(int p) { return p + (p >> 4); }
+__host__ __device__ inline int spad_h(int p) { return p + (p >> 4); }
+
+GRF_DEV float2 tw_load(const float2* __restrict__ tw, int k, int dir) {
+  const float2 w = __ldg(tw + k);
+  return dir > 0 ? w : make_float2(w.x, -w.y);
+}
+
+// One final stage of radix R < P: each thread does P/R butterflies j = tau + u TPT
+// on registers v[u + r P/R]; Ns = N/R so the twiddle is exp(DIR 2 pi i j r / N).
+template <int P, int R, int DIR>
+GRF_DEV void last_small_stage(float2 (&v)[P], int tau, int TPT, const float2* __restrict__ tw) {
+  constexpr int U = P / R;
+  static_for<0, U>([&](auto uu) {
+    constexpr int u = decltype(uu)::value;
+    const int j = tau + u * TPT;
+    static_for<1, R>([&](auto rr) {
+      constexpr int r = decltype(rr)::value;
+      v[u + r * U] = cmul(v[u + r * U], tw_load(tw, j * r, DIR));
+    });
+    dft_regs<R, DIR, U, u>(v);
+  });
+}
+
+// C sequences of length N (runtime power of two, N = TPT * P, N >= P) per CTA.
+//   v   : this thread's points (positions tau + TPT q)
+//   sm  : shared buffer of at least spad(N) * C float2 (unused if N == P)
+//   tw  : tw[k] = exp(+2 pi i k / N), k < N (FP64-built, FP32-rounded)
+// Every exchange starts with a __syncthreads(), so the caller may have used
+// `sm` just before; after return other threads may still read `sm`.
+template <int P, int DIR>
+GRF_DEV void fft_core(float2 (&v)[P], float2* sm, int tau, int c, int C, int N, int logN,
+                      const float2* __restrict__ tw) {
+  if constexpr (P == 1) {
+    return;
+  } else if constexpr (P < 16) {
+    // N == P: a single in-register stage.
+    dft_regs<P, DIR, 1, 0>(v);
+  } else {
+    const int TPT = N >> 4;
+    const int n16 = logN >> 2;
+    const int rl = logN & 3;
+    int Ns = 1;
+    for (int s = 0; s < n16; ++s) {
+      const int m = tau & (Ns - 1);
+      if (Ns > 1) {
+        const int stride = TPT / Ns;  // N / (16 Ns)
+#pragma unroll
+        for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], tw_load(tw, m * r * stride, DIR));
+      }
+      dft_regs<16, DIR, 1, 0>(v);
+      const bool last = (s == n16 - 1) && rl == 0;
+      if (!last) {
+        const int base = (tau - m) * 16 + m;  // (j / Ns) Ns 16 + j % Ns
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 16; ++r) sm[spad(base + r * Ns) * C + c] = v[r];
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = sm[spad(tau + TPT * q) * C + c];
+      }
+      Ns *= 16;
+    }
+    if (rl == 1) last_small_stage<16, 2, DIR>(v, tau, TPT, tw);
+    else if (rl == 2) last_small_stage<16, 4, DIR>(v, tau, TPT, tw);
+    else if (rl == 3) last_small_stage<16, 8, DIR>(v, tau, TPT, tw);
+  }
+}
+
+}  // namespace grf

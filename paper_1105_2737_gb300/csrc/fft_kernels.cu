@@ -1,0 +1,445 @@
+// FP32 kernels of the sampling path, its Algorithm 1 mode and its adjoint.
+//
+// Column pass (col_kernel): C consecutive columns of a plane, each a complex
+// sequence along a strided axis.  With COL_NOISE it is the first pass of
+// Algorithm 2 (§3): the kernel draws the Hermitian noise xi_K of every entry
+// of its columns in registers (Philox4x32-10 + Box-Muller, the conjugate
+// rule of Eq. conj on the planes k_d in {0, N_d/2}), multiplies by s_K
+// (rule a) / Eq. drf) and runs the inverse FFT along axis 1; the noise never
+// touches memory.
+//
+// Row pass (row_kernel): C rows along the contiguous last axis.  ROW_C2R turns
+// the half spectrum (M+1 entries) into N = 2M reals with one M-point complex
+// inverse FFT: Z[k] = (X[k] + conj X[M-k]) + i e^{2 pi i k/N} (X[k] - conj X[M-k]),
+// z = IFFT_M(Z), f[2m] = Re z[m], f[2m+1] = Im z[m].  ROW_R2C is the forward
+// counterpart (pack x[2m] + i x[2m+1], FFT_M, split).
+#include "kernels.h"
+#include "fft_core.cuh"
+
+namespace grf {
+
+// ---------------------------------------------------------------------------
+// Half-spectrum helpers
+// ---------------------------------------------------------------------------
+
+// Column index of a plane of H (axis 1 is the transform axis) -> (kmid, kd).
+struct ColGeom {
+  int kmid, kd;
+};
+GRF_DEV ColGeom col_geom(int64_t col, const HalfGeom& g) {
+  ColGeom r;
+  r.kmid = (int)(col / (g.M + 1));
+  r.kd = (int)(col - (int64_t)r.kmid * (g.M + 1));
+  return r;
+}
+
+// Folded table index of (k1, kmid, kd): S depends on |p_i| only.
+GRF_DEV int64_t fold_index(int k1, int kmid, int kd, const HalfGeom& g) {
+  const int f1 = min(k1, g.N1 - k1);
+  const int fm = min(kmid, g.Nmid - kmid);
+  return ((int64_t)f1 * (g.Nmid / 2 + 1) + fm) * (g.M + 1) + kd;
+}
+
+// xi_K at (k1, kmid, kd) of field `field`.
+GRF_DEV float2 xi_at(int k1, int kmid, int kd, int64_t field, const HalfGeom& g) {
+  const uint64_t row = (uint64_t)k1 * g.Nmid + kmid;
+  const uint64_t nrow = (uint64_t)((g.N1 - k1) & (g.N1 - 1)) * g.Nmid + ((g.Nmid - kmid) & (g.Nmid - 1));
+  return alg2_xi(row, nrow, kd, g.M, g.Q, g.seed + (uint64_t)(g.field0 + field));
+}
+
+GRF_DEV int64_t tiled_addr(int64_t pos, int64_t col, int64_t ncols, int T) {
+  if (T == 1) return pos * ncols + col;
+  return (pos / T) * (ncols * T) + col * T + (pos % T);
+}
+
+// Deterministic CTA sum of three doubles: warp shuffles, then warp 0 in order.
+GRF_DEV void block_sum3(double v0, double v1, double v2, double* out3, double* scratch) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v0 += __shfl_down_sync(0xffffffffu, v0, o);
+    v1 += __shfl_down_sync(0xffffffffu, v1, o);
+    v2 += __shfl_down_sync(0xffffffffu, v2, o);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    scratch[3 * w] = v0;
+    scratch[3 * w + 1] = v1;
+    scratch[3 * w + 2] = v2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0, c = 0;
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; ++i) {
+      a += scratch[3 * i];
+      b += scratch[3 * i + 1];
+      c += scratch[3 * i + 2];
+    }
+    out3[0] = a;
+    out3[1] = b;
+    out3[2] = c;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Column pass
+// ---------------------------------------------------------------------------
+
+template <int P, int SRC, int MODE>
+__global__ void __launch_bounds__(512) col_kernel(ColArgs a) {
+  extern __shared__ float2 sm[];
+  const int C = a.C;
+  const int t = threadIdx.x;
+  const int c = t & (C - 1);
+  const int tau = t / C;
+  const int TPT = a.N / P;
+  const int64_t col = (int64_t)blockIdx.x * C + c;
+  const bool valid = col < a.ncols;
+  const int64_t field = blockIdx.z;
+  const int64_t base = field * a.bstride + (int64_t)blockIdx.y * a.ostride;
+
+  ColGeom cg{0, 0};
+  if (SRC == COL_NOISE || MODE == COL_FWD_SCALE_INV || MODE == COL_FWD_ADJ) cg = col_geom(valid ? col : 0, a.g);
+
+  float2 v[P];
+  if constexpr (SRC == COL_NOISE) {
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const int k1 = tau + TPT * q;
+      float2 x = make_float2(0.f, 0.f);
+      if (valid) {
+        const float s = __ldg(a.g.stab + fold_index(k1, cg.kmid, cg.kd, a.g));
+        x = cscale(xi_at(k1, cg.kmid, cg.kd, field, a.g), s);
+      }
+      v[q] = x;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const int pos = tau + TPT * q;
+      v[q] = valid ? a.in[base + tiled_addr(pos, col, a.ncols, a.T)] : make_float2(0.f, 0.f);
+    }
+  }
+
+  if constexpr (MODE == COL_INV) {
+    fft_core<P, +1>(v, sm, tau, c, C, a.N, a.logN, a.tw);
+  } else {
+    fft_core<P, -1>(v, sm, tau, c, C, a.N, a.logN, a.tw);
+  }
+
+  if constexpr (MODE == COL_FWD_SCALE_INV) {
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const int k1 = tau + TPT * q;
+      const float s = valid ? __ldg(a.g.stab + fold_index(k1, cg.kmid, cg.kd, a.g)) * a.g.alg1_scale : 0.f;
+      v[q] = cscale(v[q], s);
+    }
+    fft_core<P, +1>(v, sm, tau, c, C, a.N, a.logN, a.tw);
+  }
+
+  if constexpr (MODE == COL_FWD_ADJ) {
+    // v[q] = G^ at K = (k1, kmid, kd).  Sum w_K d_theta s_K Re(xi_K conj G^_K).
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    if (valid) {
+      const float w = (cg.kd == 0 || cg.kd == a.g.M) ? 1.f : 2.f;
+      const int64_t hsz = (int64_t)(a.g.N1 / 2 + 1) * (a.g.Nmid / 2 + 1) * (a.g.M + 1);
+#pragma unroll
+      for (int q = 0; q < P; ++q) {
+        const int k1 = tau + TPT * q;
+        const int64_t fi = fold_index(k1, cg.kmid, cg.kd, a.g);
+        const float2 xi = xi_at(k1, cg.kmid, cg.kd, field, a.g);
+        const float re = w * fmaf(xi.x, v[q].x, xi.y * v[q].y);
+        a0 = fmaf(re, __ldg(a.g.stab + fi), a0);
+        a1 = fmaf(re, __ldg(a.g.dstab + fi), a1);
+        a2 = fmaf(re, __ldg(a.g.dstab + hsz + fi), a2);
+      }
+    }
+    double* scratch = reinterpret_cast<double*>(sm);
+    const int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    block_sum3((double)a0 * a.g.inv_sigma, (double)a1, (double)a2, a.partial + 3 * blk, scratch);
+    return;
+  }
+
+  if (valid) {
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const int pos = tau + TPT * q;
+      a.out[base + tiled_addr(pos, col, a.ncols, a.T)] = v[q];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Row pass
+// ---------------------------------------------------------------------------
+
+GRF_DEV int64_t hrow_addr(int64_t g, int k, int M, int T) {
+  if (T == 1) return g * (M + 1) + k;
+  return (g / T) * ((int64_t)(M + 1) * T) + (int64_t)k * T + (g % T);
+}
+
+// Z[k] of the c2r split from X[k] and X[M - k] (both in shared memory).
+GRF_DEV float2 c2r_pre(float2 X, float2 Y, float2 w) {
+  // A = X + conj Y, B = X - conj Y, Z = A + i w B
+  const float2 A = make_float2(X.x + Y.x, X.y - Y.y);
+  const float2 B = make_float2(X.x - Y.x, X.y + Y.y);
+  const float2 wB = cmul(w, B);
+  return make_float2(A.x - wB.y, A.y + wB.x);
+}
+
+// X[k] of the r2c split from Zf[k] and Zf[M - k]: 1/2 (A - i conj(w) B) with
+// A = Zk + conj Zmk, B = Zk - conj Zmk, w = exp(2 pi i k / N).
+GRF_DEV float2 r2c_post(float2 Zk, float2 Zmk, float2 w) {
+  const float2 A = make_float2(Zk.x + Zmk.x, Zk.y - Zmk.y);
+  const float2 B = make_float2(Zk.x - Zmk.x, Zk.y + Zmk.y);
+  const float2 wB = cmulc(B, w);  // B * conj(w)
+  return make_float2(0.5f * (A.x + wB.y), 0.5f * (A.y - wB.x));
+}
+
+template <int P, int SRC, int MODE>
+__global__ void __launch_bounds__(512) row_kernel(RowArgs a) {
+  extern __shared__ float2 sm[];
+  const int C = a.C;
+  const int t = threadIdx.x;
+  const int c = t & (C - 1);
+  const int tau = t / C;
+  const int M = a.M;
+  const int N = 2 * M;
+  const int TPT = M / P;
+  const int64_t g = (int64_t)blockIdx.x * C + c;
+  const bool valid = g < a.nrows;
+  const int64_t field = valid ? g / a.rows_per_field : 0;
+  const int64_t rowf = valid ? g - field * a.rows_per_field : 0;
+  float2 v[P];
+
+  if constexpr (MODE == ROW_C2R) {
+    // Stage X[0..M] of every row of the CTA in shared memory.
+    for (int k = tau; k <= M; k += TPT) {
+      float2 x = make_float2(0.f, 0.f);
+      if (valid) {
+        if constexpr (SRC == ROW_LOAD_H) {
+          x = a.inH[hrow_addr(g, k, M, a.T)];
+        } else {  // ROW_NOISE_H: d = 1, one row per field
+          const float s = __ldg(a.g.stab + k);
+          x = cscale(alg2_xi(0, 0, k, M, a.g.Q, a.g.seed + (uint64_t)(a.g.field0 + field)), s);
+        }
+      }
+      sm[spad(k) * C + c] = x;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const int k = tau + TPT * q;
+      v[q] = c2r_pre(sm[spad(k) * C + c], sm[spad(M - k) * C + c], __ldg(a.twN + k));
+    }
+    if constexpr (P < 16) __syncthreads();
+    fft_core<P, +1>(v, sm, tau, c, C, M, a.logM, a.twM);
+    if (valid) {
+      float2* o = reinterpret_cast<float2*>(a.outR + g * N);
+#pragma unroll
+      for (int q = 0; q < P; ++q) o[tau + TPT * q] = v[q];
+    }
+    return;
+  } else {
+    // Forward r2c of a real row: z[m] = x[2m] + i x[2m+1].
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const int m = tau + TPT * q;
+      float2 z = make_float2(0.f, 0.f);
+      if (valid) {
+        if constexpr (SRC == ROW_LOAD_REAL) {
+          z = reinterpret_cast<const float2*>(a.inR + g * N)[m];
+        } else {  // ROW_NOISE_REAL (Algorithm 1): flat index of the point
+          z = alg1_normal_pair((uint64_t)(rowf * N + 2 * m), a.g.seed + (uint64_t)(a.g.field0 + field));
+        }
+      }
+      v[q] = z;
+    }
+    fft_core<P, -1>(v, sm, tau, c, C, M, a.logM, a.twM);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < P; ++q) sm[spad(tau + TPT * q) * C + c] = v[q];
+    __syncthreads();
+    float2 X[P];
+    float2 XM = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const int k = tau + TPT * q;
+      const float2 Zmk = sm[spad((M - k) & (M - 1)) * C + c];
+      X[q] = r2c_post(v[q], Zmk, __ldg(a.twN + k));
+    }
+    if (tau == 0) XM = make_float2(v[0].x - v[0].y, 0.f);  // k = M: Re Z0 - Im Z0
+
+    if constexpr (MODE == ROW_R2C) {
+      if (valid) {
+#pragma unroll
+        for (int q = 0; q < P; ++q) a.outH[hrow_addr(g, tau + TPT * q, M, a.T)] = X[q];
+        if (tau == 0) a.outH[hrow_addr(g, M, M, a.T)] = XM;
+      }
+      return;
+    } else if constexpr (MODE == ROW_R2C_SCALE_C2R) {
+      // 1-D Algorithm 1: A = s_K DFT(z) / sqrt(N_tot), then c2r.
+      const float sc = a.g.alg1_scale;
+#pragma unroll
+      for (int q = 0; q < P; ++q) X[q] = cscale(X[q], __ldg(a.g.stab + tau + TPT * q) * sc);
+      if (tau == 0) XM = cscale(XM, __ldg(a.g.stab + M) * sc);
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < P; ++q) sm[spad(tau + TPT * q) * C + c] = X[q];
+      if (tau == 0) sm[spad(M) * C + c] = XM;
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < P; ++q) {
+        const int k = tau + TPT * q;
+        v[q] = c2r_pre(X[q], sm[spad(M - k) * C + c], __ldg(a.twN + k));
+      }
+      if constexpr (P < 16) __syncthreads();
+      fft_core<P, +1>(v, sm, tau, c, C, M, a.logM, a.twM);
+      if (valid) {
+        float2* o = reinterpret_cast<float2*>(a.outR + g * N);
+#pragma unroll
+        for (int q = 0; q < P; ++q) o[tau + TPT * q] = v[q];
+      }
+      return;
+    } else {  // ROW_R2C_ADJ: 1-D adjoint, one row per field
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+      if (valid) {
+        const uint64_t key = a.g.seed + (uint64_t)(a.g.field0 + field);
+#pragma unroll
+        for (int q = 0; q <= P; ++q) {
+          int k;
+          float2 G;
+          if (q < P) {
+            k = tau + TPT * q;
+            G = X[q];
+          } else {
+            if (tau != 0) break;
+            k = M;
+            G = XM;
+          }
+          const float w = (k == 0 || k == M) ? 1.f : 2.f;
+          const float2 xi = alg2_xi(0, 0, k, M, a.g.Q, key);
+          const float re = w * fmaf(xi.x, G.x, xi.y * G.y);
+          a0 = fmaf(re, __ldg(a.g.stab + k), a0);
+          a1 = fmaf(re, __ldg(a.g.dstab + k), a1);
+          a2 = fmaf(re, __ldg(a.g.dstab + (M + 1) + k), a2);
+        }
+      }
+      // per-row deterministic sum over the TPT threads of the row
+      double* sd = reinterpret_cast<double*>(sm);
+      __syncthreads();
+      sd[3 * t] = (double)a0 * a.g.inv_sigma;
+      sd[3 * t + 1] = a1;
+      sd[3 * t + 2] = a2;
+      __syncthreads();
+      if (tau == 0 && valid) {
+        double s0 = 0, s1 = 0, s2 = 0;
+        for (int u = 0; u < TPT; ++u) {
+          const int tt = u * C + c;
+          s0 += sd[3 * tt];
+          s1 += sd[3 * tt + 1];
+          s2 += sd[3 * tt + 2];
+        }
+        a.partial[3 * g] = s0;
+        a.partial[3 * g + 1] = s1;
+        a.partial[3 * g + 2] = s2;
+      }
+      return;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+
+int points_per_thread(int n) { return n >= 16 ? 16 : n; }
+
+size_t col_smem_bytes(int N, int C) {
+  size_t e = (size_t)(N >= 16 ? spad_h(N) : 0) * C * sizeof(float2);
+  const size_t red = 3 * sizeof(double) * 32;  // block_sum3 scratch
+  return e > red ? e : red;
+}
+
+size_t row_smem_bytes(int M, int C) {
+  size_t e = (size_t)(spad_h(M) + 1) * C * sizeof(float2);
+  const size_t red = 3 * sizeof(double) * 1024;  // ROW_R2C_ADJ per-thread partials
+  (void)red;
+  return e;
+}
+
+template <int P, int SRC, int MODE>
+static cudaError_t launch_col_t(const ColArgs& a, dim3 grid, cudaStream_t s) {
+  const int threads = a.C * a.N / P;
+  const size_t smem = col_smem_bytes(a.N, a.C);
+  auto k = col_kernel<P, SRC, MODE>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k<<<grid, threads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int SRC, int MODE>
+static cudaError_t launch_col_p(int P, const ColArgs& a, dim3 grid, cudaStream_t s) {
+  switch (P) {
+    case 2: return launch_col_t<2, SRC, MODE>(a, grid, s);
+    case 4: return launch_col_t<4, SRC, MODE>(a, grid, s);
+    case 8: return launch_col_t<8, SRC, MODE>(a, grid, s);
+    case 16: return launch_col_t<16, SRC, MODE>(a, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_col(int src, int mode, int P, const ColArgs& a, dim3 grid, cudaStream_t s) {
+  if (src == COL_NOISE && mode == COL_INV) return launch_col_p<COL_NOISE, COL_INV>(P, a, grid, s);
+  if (src == COL_LOAD && mode == COL_INV) return launch_col_p<COL_LOAD, COL_INV>(P, a, grid, s);
+  if (src == COL_LOAD && mode == COL_FWD) return launch_col_p<COL_LOAD, COL_FWD>(P, a, grid, s);
+  if (src == COL_LOAD && mode == COL_FWD_SCALE_INV) return launch_col_p<COL_LOAD, COL_FWD_SCALE_INV>(P, a, grid, s);
+  if (src == COL_LOAD && mode == COL_FWD_ADJ) return launch_col_p<COL_LOAD, COL_FWD_ADJ>(P, a, grid, s);
+  return cudaErrorInvalidValue;
+}
+
+template <int P, int SRC, int MODE>
+static cudaError_t launch_row_t(const RowArgs& a, dim3 grid, cudaStream_t s) {
+  const int threads = a.C * (a.M / P);
+  size_t smem = row_smem_bytes(a.M, a.C);
+  if (MODE == ROW_R2C_ADJ) {
+    const size_t need = (size_t)threads * 3 * sizeof(double);
+    if (need > smem) smem = need;
+  }
+  auto k = row_kernel<P, SRC, MODE>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k<<<grid, threads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int SRC, int MODE>
+static cudaError_t launch_row_p(int P, const RowArgs& a, dim3 grid, cudaStream_t s) {
+  switch (P) {
+    case 1: return launch_row_t<1, SRC, MODE>(a, grid, s);
+    case 2: return launch_row_t<2, SRC, MODE>(a, grid, s);
+    case 4: return launch_row_t<4, SRC, MODE>(a, grid, s);
+    case 8: return launch_row_t<8, SRC, MODE>(a, grid, s);
+    case 16: return launch_row_t<16, SRC, MODE>(a, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_row(int src, int mode, int P, const RowArgs& a, dim3 grid, cudaStream_t s) {
+  if (src == ROW_LOAD_H && mode == ROW_C2R) return launch_row_p<ROW_LOAD_H, ROW_C2R>(P, a, grid, s);
+  if (src == ROW_NOISE_H && mode == ROW_C2R) return launch_row_p<ROW_NOISE_H, ROW_C2R>(P, a, grid, s);
+  if (src == ROW_LOAD_REAL && mode == ROW_R2C) return launch_row_p<ROW_LOAD_REAL, ROW_R2C>(P, a, grid, s);
+  if (src == ROW_NOISE_REAL && mode == ROW_R2C) return launch_row_p<ROW_NOISE_REAL, ROW_R2C>(P, a, grid, s);
+  if (src == ROW_NOISE_REAL && mode == ROW_R2C_SCALE_C2R)
+    return launch_row_p<ROW_NOISE_REAL, ROW_R2C_SCALE_C2R>(P, a, grid, s);
+  if (src == ROW_LOAD_REAL && mode == ROW_R2C_ADJ) return launch_row_p<ROW_LOAD_REAL, ROW_R2C_ADJ>(P, a, grid, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace grf

@@ -1,0 +1,98 @@
+// Launch descriptors shared by the host planner and the FP32 FFT kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace grf {
+
+// Sources and modes of the column pass (complex FFT along a strided axis).
+enum ColSrc { COL_NOISE = 0, COL_LOAD = 1 };
+enum ColMode {
+  COL_INV = 0,            // inverse transform, store
+  COL_FWD = 1,            // forward transform, store
+  COL_FWD_SCALE_INV = 2,  // forward, multiply by s_K / sqrt(N_tot), inverse, store (Alg. 1)
+  COL_FWD_ADJ = 3         // forward, then reduce against regenerated xi (adjoint)
+};
+
+// Sources and modes of the row pass (the contiguous last axis).
+enum RowSrc { ROW_LOAD_H = 0, ROW_NOISE_H = 1, ROW_LOAD_REAL = 2, ROW_NOISE_REAL = 3 };
+enum RowMode {
+  ROW_C2R = 0,            // half spectrum (M+1) -> N = 2M reals
+  ROW_R2C = 1,            // N reals -> half spectrum (M+1), forward
+  ROW_R2C_SCALE_C2R = 2,  // 1-D Algorithm 1 in one pass
+  ROW_R2C_ADJ = 3         // 1-D adjoint: forward r2c, then reduce against regenerated xi
+};
+
+// Geometry of the half spectrum H = N1 x Nmid x (M + 1) (d = 3), N1 x (M + 1)
+// (d = 2, Nmid = 1) or (M + 1) (d = 1, N1 = Nmid = 1), and its noise keys.
+struct HalfGeom {
+  int d;
+  int N1, Nmid, M;        // N_d = 2 M
+  uint32_t Q;             // Philox calls per row: floor(M/2) + 1
+  uint64_t seed;          // key of field b is seed + b (+ field0)
+  int64_t field0;         // first field index of this launch
+  const float* stab;      // s_K on the folded half spectrum (N1/2+1) x (Nmid/2+1) x (M+1)
+  const float* dstab;     // d s_K / d(ell), d s_K / d(nu) (2 tables, same shape), adjoint only
+  float inv_sigma;        // d s_K / d sigma = s_K / sigma, adjoint only
+  float alg1_scale;       // 1 / sqrt(N_tot), Algorithm 1
+};
+
+struct ColArgs {
+  int N, logN;      // transform length along the axis
+  int C;            // columns per CTA (blockDim.x = C * N / P)
+  int64_t ncols;    // columns in a plane (consecutive in memory)
+  int T;            // row tile of the layout (1: plain [pos][col]; T: [pos/T][col][pos%T])
+  int64_t ostride;  // element offset between planes (gridDim.y planes)
+  int64_t bstride;  // element offset between fields (gridDim.z fields)
+  const float2* in;
+  float2* out;
+  const float2* tw;  // tw[k] = exp(2 pi i k / N)
+  int plane_is_k1;   // COL_NOISE / scale / adjoint: the transform axis is axis 1
+  HalfGeom g;
+  double* partial;   // COL_FWD_ADJ: 3 doubles per CTA, indexed by linear block id
+};
+
+struct RowArgs {
+  int M, logM;        // complex FFT length; real length N = 2 M
+  int C;              // rows per CTA (blockDim.x = C * M / P)
+  int64_t nrows;      // rows in this launch (all fields)
+  int64_t rows_per_field;
+  int T;              // tile of the half-spectrum layout (1: plain rows)
+  const float2* inH;  // ROW_LOAD_H
+  const float* inR;   // ROW_LOAD_REAL
+  float2* outH;       // ROW_R2C
+  float* outR;        // ROW_C2R, ROW_R2C_SCALE_C2R
+  const float2* twM;  // exp(2 pi i k / M), k < M
+  const float2* twN;  // exp(2 pi i k / N), k < N
+  HalfGeom g;
+  double* partial;    // ROW_R2C_ADJ
+};
+
+// Host launchers (fft_kernels.cu).  P is the points per thread of the
+// transform (16 if the length is >= 16, else the length itself).
+cudaError_t launch_col(int src, int mode, int P, const ColArgs& a, dim3 grid, cudaStream_t s);
+cudaError_t launch_row(int src, int mode, int P, const RowArgs& a, dim3 grid, cudaStream_t s);
+size_t col_smem_bytes(int N, int C);
+size_t row_smem_bytes(int M, int C);
+int points_per_thread(int n);
+
+// Table kernels (tables.cu).  All arithmetic in FP64, stored rounded to FP32.
+struct SpecParams {
+  int family;
+  double sigma, ell, nu, m;
+  int k, l, n;
+  double scale;       // multiplies S/|D| (discrete normalisation), normally 1
+  double L[3];
+  int nn[3];          // N_1..N_d
+  int d;
+};
+cudaError_t build_twiddles(float2* tw, int maxlen, cudaStream_t s);
+cudaError_t build_twiddles_d(double2* tw, int maxlen, cudaStream_t s);
+cudaError_t build_stab(float* stab, float* dstab, const SpecParams& sp, double dig_a_minus_nu,
+                       cudaStream_t s);
+cudaError_t build_stab_d(double* stab, const SpecParams& sp, cudaStream_t s);
+cudaError_t philox_words(uint64_t key, uint32_t tag, uint64_t q0, int64_t count, uint32_t* out, cudaStream_t s);
+cudaError_t reduce_partials(const double* partial, int64_t nblk_per_field, int64_t nfields,
+                            double* out, cudaStream_t s);
+
+}  // namespace grf

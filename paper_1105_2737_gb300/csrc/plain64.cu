@@ -1,0 +1,154 @@
+// Plain FP64 form of the method: one field per launch sequence, nothing fused.
+//   noise kernel (xi on the full grid, Hermitian by Eq. conj, or real z for
+//   Algorithm 1) -> HBM; scale kernel (s_K, or s_K / sqrt(N_tot) after the
+//   forward transform of Algorithm 1); radix-2 Stockham FFT, one launch per
+//   stage, along every axis over the full complex grid; real part.
+// It is the FP64 comparator of the fused FP32 path and the GRF_FP64 plans.
+#include "kernels.h"
+#include "common.cuh"
+#include "plain64.h"
+
+namespace grf {
+
+struct Full64 {
+  int d;
+  int n[3];       // N_1..N_d (unused axes = 1)
+  int M;          // N_d / 2
+  uint32_t Q;
+  int Nmid;       // N_2 for d = 3, else 1
+  int N1;         // N_1 for d >= 2, else 1
+};
+
+// Full-grid flat index -> (k1, kmid, kd) in the d = 1/2/3 convention of H.
+__device__ void split_full(int64_t idx, const Full64& f, int* k1, int* km, int* kd) {
+  const int Nd = f.n[f.d - 1];
+  *kd = (int)(idx % Nd);
+  const int64_t r = idx / Nd;
+  if (f.d == 3) {
+    *km = (int)(r % f.n[1]);
+    *k1 = (int)(r / f.n[1]);
+  } else if (f.d == 2) {
+    *km = 0;
+    *k1 = (int)r;
+  } else {
+    *km = 0;
+    *k1 = 0;
+  }
+}
+
+__global__ void noise_full_alg2(double2* x, Full64 f, uint64_t key, int64_t total) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  int k1, km, kd;
+  split_full(i, f, &k1, &km, &kd);
+  bool conj_it = false;
+  if (kd > f.M) {  // outside H: xi_K = conj xi_{-K}
+    kd = f.n[f.d - 1] - kd;
+    k1 = (f.N1 - k1) & (f.N1 - 1);
+    km = (f.Nmid - km) & (f.Nmid - 1);
+    conj_it = true;
+  }
+  const uint64_t row = (uint64_t)k1 * f.Nmid + km;
+  const uint64_t nrow = (uint64_t)((f.N1 - k1) & (f.N1 - 1)) * f.Nmid + ((f.Nmid - km) & (f.Nmid - 1));
+  double2 xi = alg2_xi_d(row, nrow, kd, f.M, f.Q, key);
+  if (conj_it) xi.y = -xi.y;
+  x[i] = xi;
+}
+
+__global__ void noise_full_alg1(double2* x, uint64_t key, int64_t total) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  x[i] = make_double2(alg1_normal_d((uint64_t)i, key), 0.0);
+}
+
+// x_K *= factor * s_K, s from the FP64 folded table.
+__global__ void scale_full(double2* x, const double* stab, Full64 f, double factor, int64_t total) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  int k1, km, kd;
+  split_full(i, f, &k1, &km, &kd);
+  const int f1 = min(k1, f.N1 - k1), fm = min(km, f.Nmid - km), fd = min(kd, f.n[f.d - 1] - kd);
+  const double s = stab[((int64_t)f1 * (f.Nmid / 2 + 1) + fm) * (f.M + 1) + fd];
+  x[i] = cscale(x[i], s * factor);
+}
+
+// One radix-2 Stockham stage along an axis of length n viewed as [outer][n][inner]:
+// butterfly j < n/2 reads j, j + n/2 and writes (j / Ns) 2 Ns + j % Ns (+ Ns).
+__global__ void stockham2_stage(const double2* __restrict__ x, double2* __restrict__ y, int n, int64_t inner,
+                                int Ns, int dir, const double2* __restrict__ tw, int64_t total) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const int64_t in = t % inner;
+  const int64_t r = t / inner;
+  const int half = n >> 1;
+  const int j = (int)(r % half);
+  const int64_t o = r / half;
+  const int64_t base = o * n * inner + in;
+  const double2 a = x[base + (int64_t)j * inner];
+  const double2 b = x[base + (int64_t)(j + half) * inner];
+  const int m = j & (Ns - 1);
+  double2 w = tw[2 * Ns + m];  // exp(2 pi i m / (2 Ns))
+  if (dir < 0) w.y = -w.y;
+  const double2 wb = cmul(w, b);
+  const int64_t od = (int64_t)((j - m) * 2 + m);
+  y[base + od * inner] = cadd(a, wb);
+  y[base + (od + Ns) * inner] = csub(a, wb);
+}
+
+__global__ void real_part(const double2* x, double* out, int64_t total) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  out[i] = x[i].x;
+}
+
+static inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+// Full complex DFT along every axis; result ends in *cur (ping-pong with *other).
+static cudaError_t fft_all_axes(double2** cur, double2** other, const Plain64Geom& g, int dir,
+                                const double2* tw, cudaStream_t s) {
+  int64_t outer = 1;
+  for (int ax = 0; ax < g.d; ++ax) {
+    const int n = g.n[ax];
+    int64_t inner = 1;
+    for (int b = ax + 1; b < g.d; ++b) inner *= g.n[b];
+    const int64_t total = outer * (n / 2) * inner;
+    for (int Ns = 1; Ns < n; Ns *= 2) {
+      stockham2_stage<<<nblk(total, 256), 256, 0, s>>>(*cur, *other, n, inner, Ns, dir, tw, total);
+      double2* t = *cur;
+      *cur = *other;
+      *other = t;
+    }
+    outer *= n;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t plain64_field(const Plain64Geom& g, int alg, uint64_t key, const double* stab, const double2* tw,
+                          double2* bufA, double2* bufB, double* out, cudaStream_t s) {
+  Full64 f{};
+  f.d = g.d;
+  for (int i = 0; i < 3; ++i) f.n[i] = i < g.d ? g.n[i] : 1;
+  f.M = g.n[g.d - 1] / 2;
+  f.Q = (uint32_t)(f.M / 2 + 1);
+  f.N1 = g.d >= 2 ? g.n[0] : 1;
+  f.Nmid = g.d == 3 ? g.n[1] : 1;
+  int64_t total = 1;
+  for (int i = 0; i < g.d; ++i) total *= g.n[i];
+  double2* cur = bufA;
+  double2* other = bufB;
+  if (alg == 2) {
+    noise_full_alg2<<<nblk(total, 256), 256, 0, s>>>(cur, f, key, total);
+    scale_full<<<nblk(total, 256), 256, 0, s>>>(cur, stab, f, 1.0, total);
+  } else {
+    noise_full_alg1<<<nblk(total, 256), 256, 0, s>>>(cur, key, total);
+    cudaError_t e = fft_all_axes(&cur, &other, g, -1, tw, s);
+    if (e != cudaSuccess) return e;
+    scale_full<<<nblk(total, 256), 256, 0, s>>>(cur, stab, f, 1.0 / sqrt((double)total), total);
+  }
+  cudaError_t e = fft_all_axes(&cur, &other, g, +1, tw, s);
+  if (e != cudaSuccess) return e;
+  real_part<<<nblk(total, 256), 256, 0, s>>>(cur, out, total);
+  return cudaGetLastError();
+}
+
+}  // namespace grf
