@@ -167,6 +167,8 @@ def run_ours(args):
     from paper_1105_2737_gb300 import _lib as L
     from paper_1105_2737_gb300.api import GRF
 
+    global BATCH
+    BATCH = args.batch
     g = GRF(SHAPE, (1.0, 1.0), max_batch=BATCH, **SPEC)
     ntot = SHAPE[0] * SHAPE[1]
     hsize = SHAPE[0] * (SHAPE[1] // 2 + 1)
@@ -232,6 +234,11 @@ def run_ours(args):
     per_pass_frac = (fields * ntot * 4 * P) / (ms / 1000.0) / 1e9 / peak / ws
     strict_frac = (fields * ntot * 4) / (ms / 1000.0) / 1e9 / peak / ws
 
+    if args.no_extras:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "fields/s", "batch": BATCH,
+                              "ms_per_step": ms / args.steps, "passes": passes}), flush=True)
+        return
     # end to end through the public API, fields delivered to pinned host memory
     host = torch.empty((BATCH,) + SHAPE, dtype=torch.float32, pin_memory=True)
     g.sample_host(seed=seed0, batch=BATCH, out=host)
@@ -324,6 +331,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--batch", type=int, default=BATCH, help="fields per step (profiling runs use a smaller batch)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the e2e, FP64 and 3-D legs")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -124,7 +124,7 @@ class _GRFFields(torch.autograd.Function):
         t = theta.detach().double().cpu().tolist()
         plan.set_params(sigma=t[0], ell=t[1], nu=t[2])
         out = plan.sample(seed, batch)
-        ctx.plan, ctx.seed, ctx.theta = plan, seed, t
+        ctx.plan, ctx.seed, ctx.theta, ctx.tdev = plan, seed, t, theta.device
         return out
 
     @staticmethod
@@ -134,7 +134,7 @@ class _GRFFields(torch.autograd.Function):
         if [cur["sigma"], cur["ell"], cur["nu"]] != ctx.theta:
             plan.set_params(sigma=ctx.theta[0], ell=ctx.theta[1], nu=ctx.theta[2])
         gp = plan.backward(ctx.seed, grad)
-        return gp.sum(dim=0).to(torch.float64), None, None, None
+        return gp.sum(dim=0).to(device=ctx.tdev, dtype=torch.float64), None, None, None
 
 
 def grf_fields(theta: torch.Tensor, plan: GRF, seed: int, batch: int) -> torch.Tensor:
