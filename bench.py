@@ -179,6 +179,7 @@ def run_ours(args):
     def step(i):
         g.sample(seed=seed0 + i * BATCH, batch=BATCH, out=out)
 
+    clk = ClockSampler(local).__enter__()  # sampling starts with the warm-up (GPU under load)
     for i in range(args.warmup):
         step(i)
     torch.cuda.synchronize()
@@ -189,12 +190,12 @@ def run_ours(args):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        e0.record(stream)
-        for i in range(args.steps):
-            step(args.warmup + i)
-        e1.record(stream)
-        torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk.__exit__()
     if ws > 1:
         torch.distributed.barrier()
     ms = e0.elapsed_time(e1)
@@ -327,8 +328,8 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--batch", type=int, default=BATCH, help="fields per step (profiling runs use a smaller batch)")

@@ -22,9 +22,11 @@
  *     the member with the larger row-major index in H;
  *   - noise is Philox4x32-10 (Salmon et al., SC'11) keyed by seed + b for
  *     field b, mapped to an exact uniform u = (2 (x >> 9) + 1) 2^-24 and to
- *     normals by Box-Muller; Algorithm 2 entry (row r, last index k_d) uses
- *     call r * (floor(N_d/4) + 1) + (k_d >> 1), counter (q_lo, q_hi, 0, 0),
- *     words 2 (k_d & 1) and 2 (k_d & 1) + 1; Algorithm 1 point j uses call
+ *     normals by Box-Muller; Algorithm 2, counter (q_lo, q_hi, 0, 0): in 1-D
+ *     entry k_d uses call k_d >> 1, words 2 (k_d & 1) and 2 (k_d & 1) + 1; in
+ *     2-D/3-D entry (k_1, k_mid, k_d) (k_mid = k_2 in 3-D, else 0) uses call
+ *     ((k_1 >> 1) N_mid + k_mid)(N_d/2 + 1) + k_d, words 2 (k_1 & 1) and
+ *     2 (k_1 & 1) + 1 (N_mid = N_2 in 3-D, else 1); Algorithm 1 point j uses call
  *     j >> 2, counter (q_lo, q_hi, 1, 0), words 2t, 2t+1 with t = (j & 3) >> 1,
  *     even j taking the cosine normal and odd j the sine normal.
  *

@@ -37,10 +37,12 @@ Conventions (the readings of the paper that this oracle fixes):
   the sequential loop of Algorithm 2, where the later iteration overwrites the
   conjugate partner written by the earlier one.
 * Noise counters: field b of a call with seed s uses key (lo, hi) of s + b.
-  Algorithm 2, half-spectrum entry in row r (linear index over k_1..k_{d-1})
-  and last index k_d: Philox call q = r * Q + (k_d >> 1) with
-  Q = floor(M/2) + 1, M = N_d/2, counter (q_lo, q_hi, 0, 0); the entry takes
-  words 2(k_d & 1) and 2(k_d & 1) + 1.  Algorithm 1, real grid point with
+  Algorithm 2, counter (q_lo, q_hi, 0, 0), M = N_d/2:
+    d = 1, entry k_d: call q = k_d >> 1, words 2(k_d & 1) and 2(k_d & 1) + 1;
+    d >= 2, entry (k_1, k_mid, k_d) (k_mid = k_2 in 3-D, 0 in 2-D, N_mid = N_2
+    or 1): call q = ((k_1 >> 1) N_mid + k_mid)(M + 1) + k_d, words 2(k_1 & 1)
+    and 2(k_1 & 1) + 1 (rows k_1 = 2i and 2i + 1 share a call).
+  Algorithm 1, real grid point with
   flat index j: call q = j >> 2, counter (q_lo, q_hi, 1, 0), pair
   t = (j & 3) >> 1 uses words 2t, 2t+1; the even j takes the cosine normal,
   the odd j the sine normal.
@@ -289,16 +291,23 @@ def independent_set_appendix(n):
 def alg2_normals(n: Sequence[int], seed: int):
     """(z_re, z_im) on H from the Philox mapping of Algorithm 2 (see module doc)."""
     hs = half_shape(n)
+    d = len(n)
     M = n[-1] // 2
-    Q = M // 2 + 1
-    rows = int(np.prod(hs[:-1])) if len(hs) > 1 else 1
-    r = np.arange(rows, dtype=np.uint64)[:, None]
-    kd = np.arange(M + 1, dtype=np.uint64)[None, :]
-    q = r * np.uint64(Q) + (kd >> np.uint64(1))
+    if d == 1:
+        kd = np.arange(M + 1, dtype=np.uint64)
+        q = kd >> np.uint64(1)
+        sel = (kd & np.uint64(1)).astype(bool)
+    else:
+        nmid = n[1] if d == 3 else 1
+        k1 = np.arange(n[0], dtype=np.uint64).reshape((-1,) + (1,) * (d - 1))
+        kmid = np.arange(nmid, dtype=np.uint64).reshape((1, -1, 1)) if d == 3 else np.uint64(0)
+        kd = np.arange(M + 1, dtype=np.uint64).reshape((1,) * (d - 1) + (-1,))
+        q = ((k1 >> np.uint64(1)) * np.uint64(nmid) + kmid) * np.uint64(M + 1) + kd
+        q = np.broadcast_to(q, hs)
+        sel = np.broadcast_to((k1 & np.uint64(1)).astype(bool), hs)
     w = philox_words(q, TAG_ALG2, seed)
-    odd = (kd & np.uint64(1)).astype(bool)
-    wa = np.where(odd, w[2], w[0])
-    wb = np.where(odd, w[3], w[1])
+    wa = np.where(sel, w[2], w[0])
+    wb = np.where(sel, w[3], w[1])
     zr, zi = box_muller(wa, wb)
     return zr.reshape(hs), zi.reshape(hs)
 

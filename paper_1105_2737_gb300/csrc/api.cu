@@ -70,7 +70,7 @@ struct RowSched {
 
 const size_t kSmemCap = 100 * 1024;
 
-ColSched choose_col(int N, int64_t ncols, int max_threads = 512) {
+ColSched choose_col(int N, int64_t ncols, int max_threads = 256) {
   ColSched s;
   s.P = points_per_thread(N);
   const int TPT = N / s.P;
@@ -83,7 +83,7 @@ ColSched choose_col(int N, int64_t ncols, int max_threads = 512) {
   return s;
 }
 
-RowSched choose_row(int M, int64_t nrows, int max_threads = 512) {
+RowSched choose_row(int M, int64_t nrows, int max_threads = 256) {
   RowSched s;
   s.P = M >= 16 ? 16 : M;
   const int TPT = M / s.P;
@@ -283,11 +283,13 @@ ColArgs col_axis1(const grf_plan_s* p, const HalfGeom& g, const float2* in, floa
   a.C = p->colA.C;
   a.ncols = (int64_t)p->Nmid * (p->M + 1);
   a.T = T;
+  a.logT = ilog2(T);
   a.ostride = 0;
   a.bstride = p->hsize;
   a.in = in;
   a.out = out;
   a.tw = twp(p, p->N1);
+  a.tws = p->tw + 2 * p->twmax;
   a.plane_is_k1 = 1;
   a.g = g;
   return a;
@@ -301,11 +303,13 @@ ColArgs col_axis2(const grf_plan_s* p, const HalfGeom& g, const float2* in, floa
   a.C = p->colB.C;
   a.ncols = p->M + 1;
   a.T = 1;
+  a.logT = 0;
   a.ostride = (int64_t)p->Nmid * (p->M + 1);
   a.bstride = p->hsize;
   a.in = in;
   a.out = out;
   a.tw = twp(p, p->Nmid);
+  a.tws = p->tw + 2 * p->twmax;
   a.plane_is_k1 = 0;
   a.g = g;
   return a;
@@ -319,8 +323,10 @@ RowArgs row_args(const grf_plan_s* p, const HalfGeom& g, int64_t nfields, int T)
   r.rows_per_field = p->ntot / p->n[p->d - 1];
   r.nrows = nfields * r.rows_per_field;
   r.T = T;
+  r.logT = ilog2(T);
   r.twM = twp(p, p->M);
   r.twN = twp(p, 2 * p->M);
+  r.tws = p->tw + 2 * p->twmax;
   r.g = g;
   return r;
 }
@@ -475,7 +481,7 @@ grf_status grf_plan_create(grf_plan* out, int d, const int64_t* n, const double*
   PLAN_CUDA(dmalloc(&p->status, 1), "status word");
   PLAN_CUDA(cudaMemset(p->status, 0, sizeof(int)), "status word");
   if (prec == GRF_FP32) {
-    PLAN_CUDA(dmalloc(&p->tw, 2 * maxlen), "twiddle table");
+    PLAN_CUDA(dmalloc(&p->tw, 2 * maxlen + kStageTableEntries), "twiddle table");
     PLAN_CUDA(build_twiddles(p->tw, (int)maxlen, s), "twiddle build");
     PLAN_CUDA(dmalloc(&p->stab, p->fold_size), "s table");
     const bool grad = spec->family <= 1 && !spec->normalize_discrete;

@@ -93,49 +93,74 @@ GRF_DEV double2 box_muller_d(uint32_t wa, uint32_t wb) {
   return make_double2(rho * c, rho * s);
 }
 
-// The normal pair of Algorithm 2 for half-spectrum entry (row r, last index kd):
-// call r * Q + (kd >> 1), words 2 (kd & 1) and 2 (kd & 1) + 1.
-GRF_DEV float2 alg2_normals(uint64_t row, int kd, uint32_t Q, uint64_t key) {
-  const u32x4 w = philox_call(row * (uint64_t)Q + (uint64_t)(kd >> 1), 0u, key);
+// Algorithm 2 noise.  1-D: entry kd uses call kd >> 1, words 2 (kd & 1), 2 (kd & 1) + 1.
+// 2-D / 3-D: entry (k1, kmid, kd) uses call ((k1 >> 1) Nmid + kmid)(M + 1) + kd,
+// words 2 (k1 & 1), 2 (k1 & 1) + 1 (rows 2i and 2i + 1 share a call).
+GRF_DEV uint64_t alg2_call_index(int k1, int kmid, int kd, int Nmid, int M) {
+  return ((uint64_t)(k1 >> 1) * (uint64_t)Nmid + (uint64_t)kmid) * (uint64_t)(M + 1) + (uint64_t)kd;
+}
+GRF_DEV float2 alg2_normals_grid(int k1, int kmid, int kd, int Nmid, int M, uint64_t key) {
+  const u32x4 w = philox_call(alg2_call_index(k1, kmid, kd, Nmid, M), 0u, key);
+  return (k1 & 1) ? box_muller(w.z, w.w) : box_muller(w.x, w.y);
+}
+GRF_DEV double2 alg2_normals_grid_d(int k1, int kmid, int kd, int Nmid, int M, uint64_t key) {
+  const u32x4 w = philox_call(alg2_call_index(k1, kmid, kd, Nmid, M), 0u, key);
+  return (k1 & 1) ? box_muller_d(w.z, w.w) : box_muller_d(w.x, w.y);
+}
+GRF_DEV float2 alg2_normals_1d(int kd, uint64_t key) {
+  const u32x4 w = philox_call((uint64_t)(kd >> 1), 0u, key);
   return (kd & 1) ? box_muller(w.z, w.w) : box_muller(w.x, w.y);
 }
-GRF_DEV double2 alg2_normals_d(uint64_t row, int kd, uint32_t Q, uint64_t key) {
-  const u32x4 w = philox_call(row * (uint64_t)Q + (uint64_t)(kd >> 1), 0u, key);
-  return (kd & 1) ? box_muller_d(w.z, w.w) : box_muller_d(w.x, w.y);
-}
 
-// Hermitian noise xi_K of Algorithm 2 at a half-spectrum entry.
-//   row  : row-major index over (k_1 .. k_{d-1}) of K
-//   nrow : the same index of -K (mod N) (only read on the planes kd in {0, M})
-//   kd   : last index, 0..M
-// Off the planes: (z_re + i z_im)/sqrt 2.  On the planes: the member of {K, -K}
-// with the larger index keeps its own normals, the other takes the conjugate;
-// a self-conjugate K (row == nrow) takes the real normal z_re.
-GRF_DEV float2 alg2_xi(uint64_t row, uint64_t nrow, int kd, int M, uint32_t Q, uint64_t key) {
+// Hermitian noise xi_K of Algorithm 2 at a half-spectrum entry (k1, kmid, kd).
+// Off the planes kd in {0, M}: (z_re + i z_im)/sqrt 2.  On the planes: the member
+// of {K, -K} with the larger row-major index keeps its own normals, the other
+// takes the conjugate; a self-conjugate K takes the real normal z_re.
+GRF_DEV float2 alg2_xi_grid(int k1, int kmid, int kd, int N1, int Nmid, int M, uint64_t key) {
   const float r2 = 0.70710678118654752440f;
   if (kd != 0 && kd != M) {
-    const float2 z = alg2_normals(row, kd, Q, key);
+    const float2 z = alg2_normals_grid(k1, kmid, kd, Nmid, M, key);
     return make_float2(z.x * r2, z.y * r2);
   }
-  if (row == nrow) {
-    const float2 z = alg2_normals(row, kd, Q, key);
-    return make_float2(z.x, 0.0f);
-  }
+  const int nk1 = (N1 - k1) & (N1 - 1), nkm = (Nmid - kmid) & (Nmid - 1);
+  const int row = k1 * Nmid + kmid, nrow = nk1 * Nmid + nkm;
+  if (row == nrow) return make_float2(alg2_normals_grid(k1, kmid, kd, Nmid, M, key).x, 0.0f);
   if (row > nrow) {
-    const float2 z = alg2_normals(row, kd, Q, key);
+    const float2 z = alg2_normals_grid(k1, kmid, kd, Nmid, M, key);
     return make_float2(z.x * r2, z.y * r2);
   }
-  const float2 z = alg2_normals(nrow, kd, Q, key);
+  const float2 z = alg2_normals_grid(nk1, nkm, kd, Nmid, M, key);
   return make_float2(z.x * r2, -z.y * r2);
 }
-GRF_DEV double2 alg2_xi_d(uint64_t row, uint64_t nrow, int kd, int M, uint32_t Q, uint64_t key) {
+GRF_DEV double2 alg2_xi_grid_d(int k1, int kmid, int kd, int N1, int Nmid, int M, uint64_t key) {
   const double r2 = 0.70710678118654752440;
-  const uint64_t src = (kd != 0 && kd != M) ? row : (row >= nrow ? row : nrow);
-  const double2 z = alg2_normals_d(src, kd, Q, key);
-  if (kd != 0 && kd != M) return make_double2(z.x * r2, z.y * r2);
-  if (row == nrow) return make_double2(z.x, 0.0);
-  if (row > nrow) return make_double2(z.x * r2, z.y * r2);
+  if (kd != 0 && kd != M) {
+    const double2 z = alg2_normals_grid_d(k1, kmid, kd, Nmid, M, key);
+    return make_double2(z.x * r2, z.y * r2);
+  }
+  const int nk1 = (N1 - k1) & (N1 - 1), nkm = (Nmid - kmid) & (Nmid - 1);
+  const int row = k1 * Nmid + kmid, nrow = nk1 * Nmid + nkm;
+  if (row == nrow) return make_double2(alg2_normals_grid_d(k1, kmid, kd, Nmid, M, key).x, 0.0);
+  if (row > nrow) {
+    const double2 z = alg2_normals_grid_d(k1, kmid, kd, Nmid, M, key);
+    return make_double2(z.x * r2, z.y * r2);
+  }
+  const double2 z = alg2_normals_grid_d(nk1, nkm, kd, Nmid, M, key);
   return make_double2(z.x * r2, -z.y * r2);
+}
+// 1-D: the self-conjugate points are kd = 0 and kd = M; everything else is generic.
+GRF_DEV float2 alg2_xi_1d(int kd, int M, uint64_t key) {
+  const float2 z = alg2_normals_1d(kd, key);
+  if (kd == 0 || kd == M) return make_float2(z.x, 0.0f);
+  const float r2 = 0.70710678118654752440f;
+  return make_float2(z.x * r2, z.y * r2);
+}
+GRF_DEV double2 alg2_xi_1d_d(int kd, int M, uint64_t key) {
+  const u32x4 w = philox_call((uint64_t)(kd >> 1), 0u, key);
+  const double2 z = (kd & 1) ? box_muller_d(w.z, w.w) : box_muller_d(w.x, w.y);
+  if (kd == 0 || kd == M) return make_double2(z.x, 0.0);
+  const double r2 = 0.70710678118654752440;
+  return make_double2(z.x * r2, z.y * r2);
 }
 
 // Real normal of Algorithm 1 at flat grid index j: call j >> 2, pair t = (j & 3) >> 1,

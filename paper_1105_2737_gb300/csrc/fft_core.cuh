@@ -142,11 +142,14 @@ GRF_DEV void last_small_stage(float2 (&v)[P], int tau, int TPT, const float2* __
 //   v   : this thread's points (positions tau + TPT q)
 //   sm  : shared buffer of at least spad(N) * C float2 (unused if N == P)
 //   tw  : tw[k] = exp(+2 pi i k / N), k < N (FP64-built, FP32-rounded)
+//   tws : radix-16 stage tables: for the stage of span Ns (16, then 256) the
+//         entries (r - 1) Ns + m = exp(+2 pi i m r / (16 Ns)), r = 1..15, m < Ns,
+//         so that the lanes of a warp (consecutive m) read consecutive entries
 // Every exchange starts with a __syncthreads(), so the caller may have used
 // `sm` just before; after return other threads may still read `sm`.
 template <int P, int DIR>
 GRF_DEV void fft_core(float2 (&v)[P], float2* sm, int tau, int c, int C, int N, int logN,
-                      const float2* __restrict__ tw) {
+                      const float2* __restrict__ tw, const float2* __restrict__ tws) {
   if constexpr (P == 1) {
     return;
   } else if constexpr (P < 16) {
@@ -156,24 +159,42 @@ GRF_DEV void fft_core(float2 (&v)[P], float2* sm, int tau, int c, int C, int N, 
     const int TPT = N >> 4;
     const int n16 = logN >> 2;
     const int rl = logN & 3;
+    // read positions tau + TPT q: spad is linear in q when TPT is a multiple of 16
+    const int rd0 = spad(tau) * C + c;
+    const int rdq = (TPT + (TPT >> 4)) * C;
     int Ns = 1;
+    int off = 0;
+    float2 w[15];  // twiddles of the next radix-16 stage, loaded one stage ahead
     for (int s = 0; s < n16; ++s) {
       const int m = tau & (Ns - 1);
       if (Ns > 1) {
-        const int stride = TPT / Ns;  // N / (16 Ns)
 #pragma unroll
-        for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], tw_load(tw, m * r * stride, DIR));
+        for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], make_float2(w[r - 1].x, DIR > 0 ? w[r - 1].y : -w[r - 1].y));
+      }
+      if (s + 1 < n16) {  // span of the next stage: 16 Ns
+        const float2* t = tws + off + (tau & (16 * Ns - 1));
+#pragma unroll
+        for (int r = 1; r < 16; ++r) w[r - 1] = __ldg(t + (r - 1) * (16 * Ns));
+        off += 15 * 16 * Ns;
       }
       dft_regs<16, DIR, 1, 0>(v);
       const bool last = (s == n16 - 1) && rl == 0;
       if (!last) {
-        const int base = (tau - m) * 16 + m;  // (j / Ns) Ns 16 + j % Ns
+        // write positions (j / Ns) Ns 16 + j % Ns + r Ns, j = tau: spad is linear in r
+        const int base = (tau - m) * 16 + m;
+        const int wr0 = spad(base) * C + c;
+        const int wrr = (Ns + (Ns >> 4)) * C;
         __syncthreads();
 #pragma unroll
-        for (int r = 0; r < 16; ++r) sm[spad(base + r * Ns) * C + c] = v[r];
+        for (int r = 0; r < 16; ++r) sm[wr0 + r * wrr] = v[r];
         __syncthreads();
+        if (TPT >= 16) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) v[q] = sm[spad(tau + TPT * q) * C + c];
+          for (int q = 0; q < 16; ++q) v[q] = sm[rd0 + q * rdq];
+        } else {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) v[q] = sm[spad(tau + TPT * q) * C + c];
+        }
       }
       Ns *= 16;
     }

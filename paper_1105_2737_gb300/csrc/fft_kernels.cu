@@ -16,6 +16,9 @@
 #include "kernels.h"
 #include "fft_core.cuh"
 
+#include <mutex>
+#include <vector>
+
 namespace grf {
 
 // ---------------------------------------------------------------------------
@@ -26,30 +29,24 @@ namespace grf {
 struct ColGeom {
   int kmid, kd;
 };
-GRF_DEV ColGeom col_geom(int64_t col, const HalfGeom& g) {
+GRF_DEV ColGeom col_geom(int col, const HalfGeom& g) {
   ColGeom r;
-  r.kmid = (int)(col / (g.M + 1));
-  r.kd = (int)(col - (int64_t)r.kmid * (g.M + 1));
+  r.kmid = col / (g.M + 1);
+  r.kd = col - r.kmid * (g.M + 1);
   return r;
 }
 
-// Folded table index of (k1, kmid, kd): S depends on |p_i| only.
-GRF_DEV int64_t fold_index(int k1, int kmid, int kd, const HalfGeom& g) {
+// Folded table index of (k1, kmid, kd): S depends on |p_i| only; the table is
+// [kd][fmid][f1] so that lanes along axis 1 read consecutive entries.
+GRF_DEV int fold_index(int k1, int kmid, int kd, const HalfGeom& g) {
   const int f1 = min(k1, g.N1 - k1);
   const int fm = min(kmid, g.Nmid - kmid);
-  return ((int64_t)f1 * (g.Nmid / 2 + 1) + fm) * (g.M + 1) + kd;
+  return (kd * (g.Nmid / 2 + 1) + fm) * (g.N1 / 2 + 1) + f1;
 }
 
 // xi_K at (k1, kmid, kd) of field `field`.
 GRF_DEV float2 xi_at(int k1, int kmid, int kd, int64_t field, const HalfGeom& g) {
-  const uint64_t row = (uint64_t)k1 * g.Nmid + kmid;
-  const uint64_t nrow = (uint64_t)((g.N1 - k1) & (g.N1 - 1)) * g.Nmid + ((g.Nmid - kmid) & (g.Nmid - 1));
-  return alg2_xi(row, nrow, kd, g.M, g.Q, g.seed + (uint64_t)(g.field0 + field));
-}
-
-GRF_DEV int64_t tiled_addr(int64_t pos, int64_t col, int64_t ncols, int T) {
-  if (T == 1) return pos * ncols + col;
-  return (pos / T) * (ncols * T) + col * T + (pos % T);
+  return alg2_xi_grid(k1, kmid, kd, g.N1, g.Nmid, g.M, g.seed + (uint64_t)(g.field0 + field));
 }
 
 // Deterministic CTA sum of three doubles: warp shuffles, then warp 0 in order.
@@ -82,6 +79,43 @@ GRF_DEV void block_sum3(double v0, double v1, double v2, double* out3, double* s
   }
 }
 
+// Normals (z_re, z_im) of Algorithm 2 for the entries (k1 = tau + TPT q, kmid, kd)
+// of this thread.  Rows k1 = 2i and 2i + 1 share one Philox call (words 0,1 and
+// 2,3).  With TPT even they sit on threads tau and tau ^ 1 (lanes t and t ^ C):
+// each draws the call for half of its rows and passes the partner its words.
+// With TPT == 1 both rows are this thread's (q and q ^ 1).
+template <int P>
+GRF_DEV void alg2_column_normals(float2 (&v)[P], int tau, int TPT, int C, int kmid, int kd,
+                                 const HalfGeom& g, uint64_t key) {
+  if (TPT == 1) {
+#pragma unroll
+    for (int i = 0; i < P / 2; ++i) {
+      const u32x4 w = philox_call(alg2_call_index(2 * i, kmid, kd, g.Nmid, g.M), 0u, key);
+      v[2 * i] = box_muller(w.x, w.y);
+      v[2 * i + 1] = box_muller(w.z, w.w);
+    }
+  } else if (C < 32) {
+    const bool odd = (tau & 1) != 0;
+#pragma unroll
+    for (int i = 0; i < P / 2; ++i) {
+      const int qa = odd ? i + P / 2 : i;  // this lane draws the call of its row qa
+      const int k1 = tau + TPT * qa;
+      const u32x4 w = philox_call(alg2_call_index(k1, kmid, kd, g.Nmid, g.M), 0u, key);
+      const uint32_t oa = odd ? w.z : w.x, ob = odd ? w.w : w.y;
+      const uint32_t pa = odd ? w.x : w.z, pb = odd ? w.y : w.w;
+      const uint32_t ra = __shfl_xor_sync(0xffffffffu, pa, C);
+      const uint32_t rb = __shfl_xor_sync(0xffffffffu, pb, C);
+      const float2 zo = box_muller(oa, ob);  // own row qa
+      const float2 zr = box_muller(ra, rb);  // own row qb, drawn by the partner
+      v[i] = odd ? zr : zo;
+      v[i + P / 2] = odd ? zo : zr;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < P; ++q) v[q] = alg2_normals_grid(tau + TPT * q, kmid, kd, g.Nmid, g.M, key);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Column pass
 // ---------------------------------------------------------------------------
@@ -94,38 +128,70 @@ __global__ void __launch_bounds__(512) col_kernel(ColArgs a) {
   const int c = t & (C - 1);
   const int tau = t / C;
   const int TPT = a.N / P;
-  const int64_t col = (int64_t)blockIdx.x * C + c;
+  const int col = blockIdx.x * C + c;
   const bool valid = col < a.ncols;
   const int64_t field = blockIdx.z;
   const int64_t base = field * a.bstride + (int64_t)blockIdx.y * a.ostride;
+  // in-field offset of (pos, col): (pos >> logT) * (ncols << logT) + (col << logT) + (pos & (T - 1))
+  const int rowstride = a.ncols << a.logT;
+  const int colpart = col << a.logT;
+  const int tmask = a.T - 1;
 
   ColGeom cg{0, 0};
   if (SRC == COL_NOISE || MODE == COL_FWD_SCALE_INV || MODE == COL_FWD_ADJ) cg = col_geom(valid ? col : 0, a.g);
 
   float2 v[P];
   if constexpr (SRC == COL_NOISE) {
+    const HalfGeom& g = a.g;
+    const uint64_t key = g.seed + (uint64_t)(g.field0 + field);
+    // s_K of this column: the folded table row (kd, fmid) is contiguous along axis 1
+    const float* srow = g.stab + (cg.kd * (g.Nmid / 2 + 1) + min(cg.kmid, g.Nmid - cg.kmid)) * (g.N1 / 2 + 1);
+    float s[P];
 #pragma unroll
     for (int q = 0; q < P; ++q) {
       const int k1 = tau + TPT * q;
-      float2 x = make_float2(0.f, 0.f);
-      if (valid) {
-        const float s = __ldg(a.g.stab + fold_index(k1, cg.kmid, cg.kd, a.g));
-        x = cscale(xi_at(k1, cg.kmid, cg.kd, field, a.g), s);
+      s[q] = __ldg(srow + min(k1, g.N1 - k1));
+    }
+    alg2_column_normals<P>(v, tau, TPT, C, cg.kmid, cg.kd, g, key);
+    const float r2 = 0.70710678118654752440f;
+    if (cg.kd != 0 && cg.kd != g.M) {
+#pragma unroll
+      for (int q = 0; q < P; ++q) v[q] = cscale(v[q], s[q] * r2);
+    } else {
+      // planes kd in {0, M}: conjugate pairs (Eq. conj) and the self-conjugate points
+      const int nkm = (g.Nmid - cg.kmid) & (g.Nmid - 1);
+#pragma unroll
+      for (int q = 0; q < P; ++q) {
+        const int k1 = tau + TPT * q;
+        const int nk1 = (g.N1 - k1) & (g.N1 - 1);
+        const int row = k1 * g.Nmid + cg.kmid, nrow = nk1 * g.Nmid + nkm;
+        float2 xi = make_float2(v[q].x * r2, v[q].y * r2);
+        if (row == nrow) {
+          xi = make_float2(v[q].x, 0.f);
+        } else if (row < nrow) {  // the partner -K carries the pair's normals
+          const float2 z = alg2_normals_grid(nk1, nkm, cg.kd, g.Nmid, g.M, key);
+          xi = make_float2(z.x * r2, -z.y * r2);
+        }
+        v[q] = cscale(xi, s[q]);
       }
-      v[q] = x;
+    }
+    if (!valid) {
+#pragma unroll
+      for (int q = 0; q < P; ++q) v[q] = make_float2(0.f, 0.f);
     }
   } else {
 #pragma unroll
     for (int q = 0; q < P; ++q) {
       const int pos = tau + TPT * q;
-      v[q] = valid ? a.in[base + tiled_addr(pos, col, a.ncols, a.T)] : make_float2(0.f, 0.f);
+      v[q] = valid ? a.in[base + (int64_t)((pos >> a.logT) * rowstride + colpart + (pos & tmask))]
+                   : make_float2(0.f, 0.f);
     }
   }
 
   if constexpr (MODE == COL_INV) {
-    fft_core<P, +1>(v, sm, tau, c, C, a.N, a.logN, a.tw);
+    fft_core<P, +1>(v, sm, tau, c, C, a.N, a.logN, a.tw, a.tws);
   } else {
-    fft_core<P, -1>(v, sm, tau, c, C, a.N, a.logN, a.tw);
+    fft_core<P, -1>(v, sm, tau, c, C, a.N, a.logN, a.tw, a.tws);
   }
 
   if constexpr (MODE == COL_FWD_SCALE_INV) {
@@ -135,7 +201,7 @@ __global__ void __launch_bounds__(512) col_kernel(ColArgs a) {
       const float s = valid ? __ldg(a.g.stab + fold_index(k1, cg.kmid, cg.kd, a.g)) * a.g.alg1_scale : 0.f;
       v[q] = cscale(v[q], s);
     }
-    fft_core<P, +1>(v, sm, tau, c, C, a.N, a.logN, a.tw);
+    fft_core<P, +1>(v, sm, tau, c, C, a.N, a.logN, a.tw, a.tws);
   }
 
   if constexpr (MODE == COL_FWD_ADJ) {
@@ -143,11 +209,11 @@ __global__ void __launch_bounds__(512) col_kernel(ColArgs a) {
     float a0 = 0.f, a1 = 0.f, a2 = 0.f;
     if (valid) {
       const float w = (cg.kd == 0 || cg.kd == a.g.M) ? 1.f : 2.f;
-      const int64_t hsz = (int64_t)(a.g.N1 / 2 + 1) * (a.g.Nmid / 2 + 1) * (a.g.M + 1);
+      const int hsz = (a.g.N1 / 2 + 1) * (a.g.Nmid / 2 + 1) * (a.g.M + 1);
 #pragma unroll
       for (int q = 0; q < P; ++q) {
         const int k1 = tau + TPT * q;
-        const int64_t fi = fold_index(k1, cg.kmid, cg.kd, a.g);
+        const int fi = fold_index(k1, cg.kmid, cg.kd, a.g);
         const float2 xi = xi_at(k1, cg.kmid, cg.kd, field, a.g);
         const float re = w * fmaf(xi.x, v[q].x, xi.y * v[q].y);
         a0 = fmaf(re, __ldg(a.g.stab + fi), a0);
@@ -165,7 +231,7 @@ __global__ void __launch_bounds__(512) col_kernel(ColArgs a) {
 #pragma unroll
     for (int q = 0; q < P; ++q) {
       const int pos = tau + TPT * q;
-      a.out[base + tiled_addr(pos, col, a.ncols, a.T)] = v[q];
+      a.out[base + (int64_t)((pos >> a.logT) * rowstride + colpart + (pos & tmask))] = v[q];
     }
   }
 }
@@ -174,9 +240,10 @@ __global__ void __launch_bounds__(512) col_kernel(ColArgs a) {
 // Row pass
 // ---------------------------------------------------------------------------
 
-GRF_DEV int64_t hrow_addr(int64_t g, int k, int M, int T) {
-  if (T == 1) return g * (M + 1) + k;
-  return (g / T) * ((int64_t)(M + 1) * T) + (int64_t)k * T + (g % T);
+// Offset of row g, entry 0 in a half-spectrum array with row tile T (a power of 2):
+// (g / T) * ((M + 1) T) + (g % T); entry k adds k T.
+GRF_DEV int64_t hrow_base(int64_t g, int M, int logT) {
+  return ((g >> logT) * (int64_t)(M + 1) << logT) + (g & ((1 << logT) - 1));
 }
 
 // Z[k] of the c2r split from X[k] and X[M - k] (both in shared memory).
@@ -214,19 +281,31 @@ __global__ void __launch_bounds__(512) row_kernel(RowArgs a) {
   float2 v[P];
 
   if constexpr (MODE == ROW_C2R) {
-    // Stage X[0..M] of every row of the CTA in shared memory.
-    for (int k = tau; k <= M; k += TPT) {
-      float2 x = make_float2(0.f, 0.f);
-      if (valid) {
-        if constexpr (SRC == ROW_LOAD_H) {
-          x = a.inH[hrow_addr(g, k, M, a.T)];
-        } else {  // ROW_NOISE_H: d = 1, one row per field
-          const float s = __ldg(a.g.stab + k);
-          x = cscale(alg2_xi(0, 0, k, M, a.g.Q, a.g.seed + (uint64_t)(a.g.field0 + field)), s);
+    // Stage X[0..M] of every row of the CTA in shared memory (all loads first).
+    const int64_t hb = hrow_base(g, M, a.logT);
+    const uint64_t key = a.g.seed + (uint64_t)(a.g.field0 + field);
+    float2 xm = make_float2(0.f, 0.f);
+    if (valid) {
+      if constexpr (SRC == ROW_LOAD_H) {
+        const float2* src = a.inH + hb;
+#pragma unroll
+        for (int q = 0; q < P; ++q) v[q] = src[(int64_t)(tau + TPT * q) << a.logT];
+        if (tau == 0) xm = src[(int64_t)M << a.logT];
+      } else {  // ROW_NOISE_H: d = 1, one row per field
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+          const int k = tau + TPT * q;
+          v[q] = cscale(alg2_xi_1d(k, M, key), __ldg(a.g.stab + k));
         }
+        if (tau == 0) xm = cscale(alg2_xi_1d(M, M, key), __ldg(a.g.stab + M));
       }
-      sm[spad(k) * C + c] = x;
+    } else {
+#pragma unroll
+      for (int q = 0; q < P; ++q) v[q] = make_float2(0.f, 0.f);
     }
+#pragma unroll
+    for (int q = 0; q < P; ++q) sm[spad(tau + TPT * q) * C + c] = v[q];
+    if (tau == 0) sm[spad(M) * C + c] = xm;
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < P; ++q) {
@@ -234,7 +313,7 @@ __global__ void __launch_bounds__(512) row_kernel(RowArgs a) {
       v[q] = c2r_pre(sm[spad(k) * C + c], sm[spad(M - k) * C + c], __ldg(a.twN + k));
     }
     if constexpr (P < 16) __syncthreads();
-    fft_core<P, +1>(v, sm, tau, c, C, M, a.logM, a.twM);
+    fft_core<P, +1>(v, sm, tau, c, C, M, a.logM, a.twM, a.tws);
     if (valid) {
       float2* o = reinterpret_cast<float2*>(a.outR + g * N);
 #pragma unroll
@@ -243,6 +322,7 @@ __global__ void __launch_bounds__(512) row_kernel(RowArgs a) {
     return;
   } else {
     // Forward r2c of a real row: z[m] = x[2m] + i x[2m+1].
+    const uint64_t key = a.g.seed + (uint64_t)(a.g.field0 + field);
 #pragma unroll
     for (int q = 0; q < P; ++q) {
       const int m = tau + TPT * q;
@@ -251,12 +331,12 @@ __global__ void __launch_bounds__(512) row_kernel(RowArgs a) {
         if constexpr (SRC == ROW_LOAD_REAL) {
           z = reinterpret_cast<const float2*>(a.inR + g * N)[m];
         } else {  // ROW_NOISE_REAL (Algorithm 1): flat index of the point
-          z = alg1_normal_pair((uint64_t)(rowf * N + 2 * m), a.g.seed + (uint64_t)(a.g.field0 + field));
+          z = alg1_normal_pair((uint64_t)(rowf * N + 2 * m), key);
         }
       }
       v[q] = z;
     }
-    fft_core<P, -1>(v, sm, tau, c, C, M, a.logM, a.twM);
+    fft_core<P, -1>(v, sm, tau, c, C, M, a.logM, a.twM, a.tws);
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < P; ++q) sm[spad(tau + TPT * q) * C + c] = v[q];
@@ -273,9 +353,10 @@ __global__ void __launch_bounds__(512) row_kernel(RowArgs a) {
 
     if constexpr (MODE == ROW_R2C) {
       if (valid) {
+        const int64_t hb = hrow_base(g, M, a.logT);
 #pragma unroll
-        for (int q = 0; q < P; ++q) a.outH[hrow_addr(g, tau + TPT * q, M, a.T)] = X[q];
-        if (tau == 0) a.outH[hrow_addr(g, M, M, a.T)] = XM;
+        for (int q = 0; q < P; ++q) a.outH[hb + ((int64_t)(tau + TPT * q) << a.logT)] = X[q];
+        if (tau == 0) a.outH[hb + ((int64_t)M << a.logT)] = XM;
       }
       return;
     } else if constexpr (MODE == ROW_R2C_SCALE_C2R) {
@@ -295,7 +376,7 @@ __global__ void __launch_bounds__(512) row_kernel(RowArgs a) {
         v[q] = c2r_pre(X[q], sm[spad(M - k) * C + c], __ldg(a.twN + k));
       }
       if constexpr (P < 16) __syncthreads();
-      fft_core<P, +1>(v, sm, tau, c, C, M, a.logM, a.twM);
+      fft_core<P, +1>(v, sm, tau, c, C, M, a.logM, a.twM, a.tws);
       if (valid) {
         float2* o = reinterpret_cast<float2*>(a.outR + g * N);
 #pragma unroll
@@ -305,7 +386,6 @@ __global__ void __launch_bounds__(512) row_kernel(RowArgs a) {
     } else {  // ROW_R2C_ADJ: 1-D adjoint, one row per field
       float a0 = 0.f, a1 = 0.f, a2 = 0.f;
       if (valid) {
-        const uint64_t key = a.g.seed + (uint64_t)(a.g.field0 + field);
 #pragma unroll
         for (int q = 0; q <= P; ++q) {
           int k;
@@ -319,7 +399,7 @@ __global__ void __launch_bounds__(512) row_kernel(RowArgs a) {
             G = XM;
           }
           const float w = (k == 0 || k == M) ? 1.f : 2.f;
-          const float2 xi = alg2_xi(0, 0, k, M, a.g.Q, key);
+          const float2 xi = alg2_xi_1d(k, M, key);
           const float re = w * fmaf(xi.x, G.x, xi.y * G.y);
           a0 = fmaf(re, __ldg(a.g.stab + k), a0);
           a1 = fmaf(re, __ldg(a.g.dstab + k), a1);
@@ -369,15 +449,51 @@ size_t row_smem_bytes(int M, int C) {
   return e;
 }
 
+// Shared-memory carveout: ask for what the resident CTAs need and leave the
+// rest of the SM's 256 KB to L1, which holds the twiddle tables (a maximal
+// carveout starves L1 and sends every twiddle load to L2).
+static cudaError_t prepare_kernel(const void* k, int threads, size_t smem) {
+  struct Entry {
+    const void* k;
+    int threads;
+    size_t smem;
+  };
+  static std::mutex mu;
+  static std::vector<Entry> done;
+  std::lock_guard<std::mutex> lock(mu);
+  for (const Entry& e : done)
+    if (e.k == k && e.threads == threads && e.smem == smem) return cudaSuccess;
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, k);
+  if (e != cudaSuccess) return e;
+  const int regs = fa.numRegs > 0 ? fa.numRegs : 1;
+  const int warps = (threads + 31) / 32;
+  int blocks = 65536 / (warps * 32 * ((regs + 7) / 8 * 8));
+  blocks = blocks < 1 ? 1 : blocks;
+  blocks = blocks > 2048 / threads ? 2048 / threads : blocks;
+  const size_t per = smem + fa.sharedSizeBytes + 1024;
+  size_t need = per * blocks;
+  const size_t cap = 228 * 1024;
+  while (need > cap && blocks > 1) need = per * --blocks;
+  int pct = (int)((need * 100 + cap - 1) / cap);
+  pct = pct < 0 ? 0 : (pct > 100 ? 100 : pct);
+  if (smem > 48 * 1024) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  if (e != cudaSuccess) return e;
+  done.push_back(Entry{k, threads, smem});
+  return cudaSuccess;
+}
+
 template <int P, int SRC, int MODE>
 static cudaError_t launch_col_t(const ColArgs& a, dim3 grid, cudaStream_t s) {
   const int threads = a.C * a.N / P;
   const size_t smem = col_smem_bytes(a.N, a.C);
   auto k = col_kernel<P, SRC, MODE>;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  cudaError_t e = prepare_kernel((const void*)k, threads, smem);
+  if (e != cudaSuccess) return e;
   k<<<grid, threads, smem, s>>>(a);
   return cudaGetLastError();
 }
@@ -411,10 +527,8 @@ static cudaError_t launch_row_t(const RowArgs& a, dim3 grid, cudaStream_t s) {
     if (need > smem) smem = need;
   }
   auto k = row_kernel<P, SRC, MODE>;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  cudaError_t e = prepare_kernel((const void*)k, threads, smem);
+  if (e != cudaSuccess) return e;
   k<<<grid, threads, smem, s>>>(a);
   return cudaGetLastError();
 }

@@ -31,7 +31,7 @@ struct HalfGeom {
   uint32_t Q;             // Philox calls per row: floor(M/2) + 1
   uint64_t seed;          // key of field b is seed + b (+ field0)
   int64_t field0;         // first field index of this launch
-  const float* stab;      // s_K on the folded half spectrum (N1/2+1) x (Nmid/2+1) x (M+1)
+  const float* stab;      // s_K on the folded half spectrum, [kd][fmid][f1]: (M+1) x (Nmid/2+1) x (N1/2+1)
   const float* dstab;     // d s_K / d(ell), d s_K / d(nu) (2 tables, same shape), adjoint only
   float inv_sigma;        // d s_K / d sigma = s_K / sigma, adjoint only
   float alg1_scale;       // 1 / sqrt(N_tot), Algorithm 1
@@ -41,12 +41,13 @@ struct ColArgs {
   int N, logN;      // transform length along the axis
   int C;            // columns per CTA (blockDim.x = C * N / P)
   int64_t ncols;    // columns in a plane (consecutive in memory)
-  int T;            // row tile of the layout (1: plain [pos][col]; T: [pos/T][col][pos%T])
+  int T, logT;      // row tile of the layout (1: plain [pos][col]; T: [pos/T][col][pos%T]), a power of 2
   int64_t ostride;  // element offset between planes (gridDim.y planes)
   int64_t bstride;  // element offset between fields (gridDim.z fields)
   const float2* in;
   float2* out;
-  const float2* tw;  // tw[k] = exp(2 pi i k / N)
+  const float2* tw;   // tw[k] = exp(2 pi i k / N)
+  const float2* tws;  // radix-16 stage tables (see fft_core)
   int plane_is_k1;   // COL_NOISE / scale / adjoint: the transform axis is axis 1
   HalfGeom g;
   double* partial;   // COL_FWD_ADJ: 3 doubles per CTA, indexed by linear block id
@@ -57,13 +58,14 @@ struct RowArgs {
   int C;              // rows per CTA (blockDim.x = C * M / P)
   int64_t nrows;      // rows in this launch (all fields)
   int64_t rows_per_field;
-  int T;              // tile of the half-spectrum layout (1: plain rows)
+  int T, logT;        // tile of the half-spectrum layout (1: plain rows), a power of 2
   const float2* inH;  // ROW_LOAD_H
   const float* inR;   // ROW_LOAD_REAL
   float2* outH;       // ROW_R2C
   float* outR;        // ROW_C2R, ROW_R2C_SCALE_C2R
   const float2* twM;  // exp(2 pi i k / M), k < M
   const float2* twN;  // exp(2 pi i k / N), k < N
+  const float2* tws;  // radix-16 stage tables (see fft_core)
   HalfGeom g;
   double* partial;    // ROW_R2C_ADJ
 };
@@ -86,6 +88,9 @@ struct SpecParams {
   int nn[3];          // N_1..N_d
   int d;
 };
+// tw[L + k] = exp(2 pi i k / L) for powers of two L <= maxlen, then (at
+// offset 2 maxlen) the radix-16 stage tables of spans 16 and 256 (15 Ns entries each).
+constexpr int kStageTableEntries = 15 * 16 + 15 * 256;
 cudaError_t build_twiddles(float2* tw, int maxlen, cudaStream_t s);
 cudaError_t build_twiddles_d(double2* tw, int maxlen, cudaStream_t s);
 cudaError_t build_stab(float* stab, float* dstab, const SpecParams& sp, double dig_a_minus_nu,

@@ -48,9 +48,7 @@ __global__ void noise_full_alg2(double2* x, Full64 f, uint64_t key, int64_t tota
     km = (f.Nmid - km) & (f.Nmid - 1);
     conj_it = true;
   }
-  const uint64_t row = (uint64_t)k1 * f.Nmid + km;
-  const uint64_t nrow = (uint64_t)((f.N1 - k1) & (f.N1 - 1)) * f.Nmid + ((f.Nmid - km) & (f.Nmid - 1));
-  double2 xi = alg2_xi_d(row, nrow, kd, f.M, f.Q, key);
+  double2 xi = f.d == 1 ? alg2_xi_1d_d(kd, f.M, key) : alg2_xi_grid_d(k1, km, kd, f.N1, f.Nmid, f.M, key);
   if (conj_it) xi.y = -xi.y;
   x[i] = xi;
 }
@@ -68,7 +66,7 @@ __global__ void scale_full(double2* x, const double* stab, Full64 f, double fact
   int k1, km, kd;
   split_full(i, f, &k1, &km, &kd);
   const int f1 = min(k1, f.N1 - k1), fm = min(km, f.Nmid - km), fd = min(kd, f.n[f.d - 1] - kd);
-  const double s = stab[((int64_t)f1 * (f.Nmid / 2 + 1) + fm) * (f.M + 1) + fd];
+  const double s = stab[((int64_t)fd * (f.Nmid / 2 + 1) + fm) * (f.N1 / 2 + 1) + f1];
   x[i] = cscale(x[i], s * factor);
 }
 

@@ -1,8 +1,8 @@
 // Plan-time tables, computed in FP64 on the device and rounded to FP32:
 //  * twiddles exp(2 pi i k / L) for every power of two L up to a maximum,
 //    stored at tw[L + k] (k < L);
-//  * s_K = sqrt(S(p_K) / |D|) on the folded half spectrum
-//    (N_1/2+1) x (N_2/2+1) x (N_d/2+1) (S depends on |p_i| only; §2 rules a), e),
+//  * s_K = sqrt(S(p_K) / |D|) on the folded half spectrum, stored
+//    (N_d/2+1) x (N_2/2+1) x (N_1/2+1) with axis 1 fastest (S depends on |p_i| only; §2 rules a), e),
 //    Eq. drf), and for the adjoint d s_K / d ell and d s_K / d nu.
 #include "kernels.h"
 #include "common.cuh"
@@ -38,9 +38,23 @@ __global__ void twiddle_kernel_d(double2* tw, int total) {
   tw[i] = make_double2(c, s);
 }
 
+// Stage tables: span Ns = 16 (240 entries) then Ns = 256 (3840 entries);
+// entry (r - 1) Ns + m = exp(2 pi i m r / (16 Ns)), r = 1..15, m < Ns.
+__global__ void stage_table_kernel(float2* tws) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kStageTableEntries) return;
+  const int Ns = i < 240 ? 16 : 256;
+  const int loc = i < 240 ? i : i - 240;
+  const int r = loc / Ns + 1, m = loc % Ns;
+  double sn, cs;
+  sincospi(2.0 * (double)(m * r) / (double)(16 * Ns), &sn, &cs);
+  tws[i] = make_float2((float)cs, (float)sn);
+}
+
 cudaError_t build_twiddles(float2* tw, int maxlen, cudaStream_t s) {
   const int total = 2 * maxlen;
   twiddle_kernel<<<(total + 255) / 256, 256, 0, s>>>(tw, total);
+  stage_table_kernel<<<(kStageTableEntries + 255) / 256, 256, 0, s>>>(tw + total);
   return cudaGetLastError();
 }
 
@@ -62,12 +76,14 @@ struct DevSpec {
   double sigma;
 };
 
-// S(p)/|D| * scale and its log-derivatives at one folded entry.
+// S(p)/|D| * scale and its log-derivatives at one folded entry.  The table is
+// stored [kd][fmid][f1] (axis 1 fastest): the column kernels, whose lanes run
+// along axis 1, then read consecutive entries.
 __device__ void spectral_entry(const DevSpec& sp, int64_t idx, double* S, double* dl, double* dn) {
-  const int i2 = (int)(idx % sp.F[2]);
-  const int64_t r = idx / sp.F[2];
+  const int i0 = (int)(idx % sp.F[0]);
+  const int64_t r = idx / sp.F[0];
   const int i1 = (int)(r % sp.F[1]);
-  const int i0 = (int)(r / sp.F[1]);
+  const int i2 = (int)(r / sp.F[1]);
   const int f[3] = {i0, i1, i2};
   double p[3] = {0, 0, 0};
   double p2 = 0.0;
