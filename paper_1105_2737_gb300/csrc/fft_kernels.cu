@@ -17,7 +17,6 @@
 #include "fft_core.cuh"
 
 #include <mutex>
-#include <vector>
 
 namespace grf {
 
@@ -458,11 +457,14 @@ static cudaError_t prepare_kernel(const void* k, int threads, size_t smem) {
     int threads;
     size_t smem;
   };
+  // a fixed table (no host allocation on the launch path); when full, the
+  // attributes are simply set again on every launch of an unseen configuration
   static std::mutex mu;
-  static std::vector<Entry> done;
+  static Entry done[512];
+  static int ndone = 0;
   std::lock_guard<std::mutex> lock(mu);
-  for (const Entry& e : done)
-    if (e.k == k && e.threads == threads && e.smem == smem) return cudaSuccess;
+  for (int i = 0; i < ndone; ++i)
+    if (done[i].k == k && done[i].threads == threads && done[i].smem == smem) return cudaSuccess;
   cudaFuncAttributes fa;
   cudaError_t e = cudaFuncGetAttributes(&fa, k);
   if (e != cudaSuccess) return e;
@@ -483,7 +485,7 @@ static cudaError_t prepare_kernel(const void* k, int threads, size_t smem) {
   }
   e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
   if (e != cudaSuccess) return e;
-  done.push_back(Entry{k, threads, smem});
+  if (ndone < 512) done[ndone++] = Entry{k, threads, smem};
   return cudaSuccess;
 }
 
