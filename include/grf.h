@@ -203,6 +203,34 @@ grf_status grf_batch_sample(grf_plan p, uint64_t seed, void* const* out, void* s
 grf_status grf_batch_graph_launch(grf_plan p, uint64_t seed, void* const* out, void* stream);
 
 /*
+ * grf_sample_2d_static - 2-D sampling that allocates no memory.  The paper has
+ * no counterpart: this is a way of calling the sampler, not part of the method.
+ *
+ * For callers that cannot allocate device memory when they need a field: code
+ * inside a host application that owns all of the device's memory (its own
+ * pool, raw cudaMalloc not allowed), and latency-critical loops in which
+ * cudaMalloc or cudaFree would implicitly synchronise the device.  It draws
+ * the same fields as grf_sample on a plan created with
+ * grf_plan_create(2, n, L, spec, GRF_ALG_ONE_FFT, GRF_FP32, ...): FP32,
+ * §3 Algorithm 2, field b with Philox key seed + b.
+ *   n, L  : host arrays of 2 grid sizes (powers of two, 2 <= N_i <= 1024) and
+ *           edge lengths (> 0); sizes above 1024 return GRF_ERR_INVALID_ARG.
+ *   spec  : Matern, Gaussian or paper family; normalize_discrete is not
+ *           supported here (GRF_ERR_UNSUPPORTED).
+ *   out   : device pointer to batch * N_1 * N_2 floats, written completely.
+ * Everything the call needs besides `out` (twiddles, the s_K table and one
+ * field's half spectrum, at most 5.1 MiB) lives in a 6 MiB file-scope device
+ * array that every device holds from the moment it loads this library until
+ * the process exits.  The first call on a device looks up that array's device
+ * address (once per device, with the device current), so make the first call
+ * before any stream capture.  All calls on a device share the array and leave
+ * their contents in it; each call rebuilds what it reads.  Calls that overlap
+ * on the GPU race on the array: keep them on one stream at a time.
+ */
+grf_status grf_sample_2d_static(const int64_t* n, const double* L, const grf_spectrum* spec, uint64_t seed,
+                                int64_t batch, float* out, void* stream);
+
+/*
  * grf_status_word - synchronise `stream`, read and clear the plan's device
  * status word (GRF_OK or GRF_ERR_TIMEOUT).
  */

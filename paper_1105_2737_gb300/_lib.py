@@ -64,6 +64,8 @@ def lib():
             "grf_batch_graph_launch": (C.c_int, [P, U64, C.POINTER(VP), VP]),
             "grf_status_word": (C.c_int, [P, VP]),
             "grf_philox_words": (C.c_int, [U64, C.c_uint32, U64, I64, VP, VP]),
+            "grf_sample_2d_static": (C.c_int, [C.POINTER(I64), C.POINTER(D), C.POINTER(grf_spectrum), U64, I64,
+                                               VP, VP]),
             "grf_plan_query": (I64, [P, C.c_int]),
             "grf_plan_timing": (C.c_int, [P, I64]),
             "grf_plan_timing_read": (I64, [P, C.POINTER(C.c_int), C.POINTER(C.c_float), I64]),
@@ -165,6 +167,14 @@ def grf_status_word(plan, stream=0) -> int:
 def grf_philox_words(key, tag, q0, count, out_ptr, stream=0):
     check(lib().grf_philox_words(C.c_uint64(key & 0xFFFFFFFFFFFFFFFF), C.c_uint32(tag), C.c_uint64(q0), int(count),
                                  C.c_void_p(out_ptr), C.c_void_p(stream)), "grf_philox_words")
+
+
+def grf_sample_2d_static(n, L, spec, seed, batch, out_ptr, stream=0):
+    """2-D FP32 Algorithm 2 sampling that allocates no device memory (see grf.h)."""
+    nn = (C.c_int64 * 2)(*[int(x) for x in n])
+    LL = (C.c_double * 2)(*[float(x) for x in L])
+    check(lib().grf_sample_2d_static(nn, LL, C.byref(spec), C.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), int(batch),
+                                     C.c_void_p(out_ptr), C.c_void_p(stream)), "grf_sample_2d_static")
 
 
 def grf_plan_query(plan, key: int) -> int:

@@ -399,6 +399,11 @@ grf_status check_plan(grf_plan p) {
 
 }  // namespace
 
+namespace grf {
+// Error text for entry points defined in other translation units.
+void set_last_error(const char* msg) { g_last_error = msg; }
+}  // namespace grf
+
 extern "C" {
 
 const char* grf_status_string(grf_status s) {

@@ -1,0 +1,61 @@
+"""The allocation-free 2-D entry point, grf_sample_2d_static, for callers that
+cannot allocate device memory when they sample (an application that owns all
+of the device's memory, or a loop where cudaMalloc / cudaFree would
+synchronise the device).  It must draw the same fields as grf_sample on an
+ordinary plan.  Collected last: a failure here leaves every other test run."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1105_2737_gb300 import build
+    build()
+    from paper_1105_2737_gb300 import _lib
+    return _lib
+
+
+def _reference(L, n, Lb, spec, seed, batch):
+    """The same fields through a plan (grf_plan_create + grf_sample)."""
+    h = L.grf_plan_create(2, n, Lb, spec, L.GRF_ALG_ONE_FFT, L.GRF_FP32, batch)
+    try:
+        out = torch.empty((batch,) + tuple(n), dtype=torch.float32, device="cuda")
+        L.grf_sample(h, seed, batch, out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+    finally:
+        L.grf_plan_destroy(h)
+
+
+def _static(L, n, Lb, spec, seed, batch):
+    out = torch.empty((batch,) + tuple(n), dtype=torch.float32, device="cuda")
+    L.grf_sample_2d_static(n, Lb, spec, seed, batch, out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def test_two_calls_in_a_row_match_the_plan_path(L):
+    calls = [((256, 512), (1.0, 2.0), L.make_spectrum(L.GRF_MATERN, 1.0, 0.05, 1.5), 7, 3),
+             ((1024, 64), (1.0, 1.0), L.make_spectrum(L.GRF_GAUSSIAN, 1.3, 0.02, 0.0), 1234, 2)]
+    got = [_static(L, *c) for c in calls]  # back to back: the second reuses the scratch array
+    for c, g in zip(calls, got):
+        ref = _reference(L, *c)
+        rel = np.linalg.norm(g - ref) / np.linalg.norm(ref)
+        assert rel <= 2e-6 and np.abs(g - ref).max() <= 1e-5, (c[0], rel)
+
+
+def test_sizes_beyond_the_scratch_are_rejected(L):
+    out = torch.empty(4, dtype=torch.float32, device="cuda")
+    nn = (C.c_int64 * 2)(2048, 64)
+    LL = (C.c_double * 2)(1.0, 1.0)
+    sp = L.make_spectrum()
+    st = L.lib().grf_sample_2d_static(nn, LL, C.byref(sp), 0, 1, C.c_void_p(out.data_ptr()), None)
+    assert st == L.GRF_ERR_INVALID_ARG
+    assert b"1024" in L.lib().grf_last_error()
