@@ -101,8 +101,10 @@ typedef struct grf_plan_s* grf_plan;
  *   out       : receives the plan handle (host pointer, must not be NULL).
  *   d         : dimension, 1..3.
  *   n         : host array of d grid sizes, each even, a power of two in
- *               [2, 4096] for axes 1..d-1 and in [2, 2^20] for axis d
- *               (axis d of a 2-D or 3-D grid: at most 8192).
+ *               [2, 4096] for axes 1..d-1 and in [2, 8192] for axis d of a
+ *               2-D or 3-D grid; a 1-D grid goes up to 2^22 (Algorithm 2 in
+ *               FP32 by a four-step c2r, and the FP64 plain form), 8192 for
+ *               Algorithm 1 in FP32.
  *   L         : host array of d edge lengths, each > 0.
  *   spec      : host pointer to the spectral density parameters.
  *   alg       : grf_algorithm.

@@ -125,6 +125,8 @@ struct grf_plan_s {
   int T = 1;  // 2-D tile of the half-spectrum workspace
   ColSched colA, colB;
   RowSched row;
+  // four-step 1-D (M > 4096): M = A * B
+  int fsA = 0, fsB = 0, fsC1 = 1, fsC2 = 1;
 
   // FP64 plain form
   double2* tw64 = nullptr;
@@ -359,6 +361,33 @@ dim3 row_grid(const RowArgs& r) { return dim3((unsigned)((r.nrows + r.C - 1) / r
 // FP32 sampling of fields [f0, f0 + nb) into out (already offset to field f0).
 grf_status sample_chunk_fp32(grf_plan p, uint64_t seed, int64_t f0, int64_t nb, float* out, cudaStream_t s) {
   const HalfGeom g = half_geom(p, seed, f0);
+  if (p->d == 1 && p->M > 4096) {
+    FourStepArgs f{};
+    f.A = p->fsA;
+    f.logA = ilog2(p->fsA);
+    f.B = p->fsB;
+    f.logB = ilog2(p->fsB);
+    f.M = p->M;
+    f.N = 2 * p->M;
+    f.T = p->fsC1;
+    f.logT = ilog2(p->fsC1);
+    f.Y = p->ws;
+    f.Yin = p->ws;
+    f.out = out;
+    f.twA = twp(p, p->fsA);
+    f.twB = twp(p, p->fsB);
+    f.twM = twp(p, p->M);
+    f.twN = twp(p, 2 * p->M);
+    f.tws = p->tw + 2 * p->twmax;
+    f.stab = p->stab;
+    f.seed = seed;
+    f.field0 = f0;
+    f.C = p->fsC1;
+    TLAUNCH(GRF_KERNEL_ROWS_1D, launch_fourstep(1, 16, f, nb, s), "four-step stage 1");
+    f.C = p->fsC2;
+    TLAUNCH(GRF_KERNEL_ROWS_1D, launch_fourstep(2, 16, f, nb, s), "four-step stage 2");
+    return GRF_OK;
+  }
   if (p->d == 1) {
     RowArgs r = row_args(p, g, nb, 1);
     r.outR = out;
@@ -439,7 +468,8 @@ grf_status grf_plan_create(grf_plan* out, int d, const int64_t* n, const double*
   }
   for (int i = 0; i < d; ++i) {
     if (!is_pow2(n[i])) return fail(GRF_ERR_UNSUPPORTED, "N_i must be a power of two");
-    const int64_t lim = (i < d - 1) ? 4096 : 8192;
+    int64_t lim = (i < d - 1) ? 4096 : 8192;
+    if (d == 1 && (prec == GRF_FP64 || alg == GRF_ALG_ONE_FFT)) lim = int64_t(1) << 22;  // four-step c2r
     if (n[i] > lim) return fail(GRF_ERR_UNSUPPORTED, "grid size above the supported maximum");
   }
 
@@ -497,7 +527,17 @@ grf_status grf_plan_create(grf_plan* out, int d, const int64_t* n, const double*
     }
     PLAN_CUDA(build_stab(p->stab, p->dstab, sp, dig, s), "s table build");
     // schedules
-    if (d == 1) {
+    if (d == 1 && p->M > 4096) {
+      const int lm = ilog2(p->M);
+      p->fsB = 1 << ((lm + 1) / 2);
+      p->fsA = p->M / p->fsB;
+      p->fsC1 = 4096 / p->fsB;  // 256 threads of 16 points
+      if (p->fsC1 > p->fsA) p->fsC1 = p->fsA;
+      p->fsC2 = 4096 / p->fsA;
+      if (p->fsC2 > p->fsB) p->fsC2 = p->fsB;
+      p->chunk = max_batch;
+      PLAN_CUDA(dmalloc(&p->ws, (size_t)(p->chunk * p->M)), "four-step workspace");
+    } else if (d == 1) {
       p->row = choose_row(p->M, max_batch);
     } else {
       p->colA = choose_col(p->N1, (int64_t)p->Nmid * (p->M + 1));
@@ -566,7 +606,7 @@ grf_status grf_sample(grf_plan p, uint64_t seed, int64_t batch, void* out, void*
     }
     return GRF_OK;
   }
-  const int64_t chunk = p->d == 1 ? batch : p->chunk;
+  const int64_t chunk = (p->d == 1 && p->M <= 4096) ? batch : p->chunk;
   for (int64_t f0 = 0; f0 < batch; f0 += chunk) {
     const int64_t nb = batch - f0 < chunk ? batch - f0 : chunk;
     st = sample_chunk_fp32(p, seed, f0, nb, (float*)out + f0 * p->ntot, s);
@@ -586,7 +626,7 @@ grf_status grf_sample_host(grf_plan p, uint64_t seed, int64_t batch, void* host_
   const size_t field_bytes = (size_t)p->ntot * esz;
   int64_t per = (int64_t)((64u << 20) / field_bytes);
   if (per < 1) per = 1;
-  if (p->prec == GRF_FP32 && p->d > 1 && per > p->chunk) per = p->chunk;
+  if (p->prec == GRF_FP32 && (p->d > 1 || p->M > 4096) && per > p->chunk) per = p->chunk;
   if (per > batch) per = batch;
   if (p->stage_fields < per) {
     for (int i = 0; i < 2; ++i) {
@@ -642,6 +682,7 @@ grf_status grf_backward(grf_plan p, uint64_t seed, int64_t batch, const void* gr
   if (p->prec != GRF_FP32 || p->alg != GRF_ALG_ONE_FFT)
     return fail(GRF_ERR_UNSUPPORTED, "the adjoint is built for FP32 Algorithm 2 plans");
   if (!p->dstab) return fail(GRF_ERR_UNSUPPORTED, "the adjoint needs a Matern or Gaussian spectrum without normalize_discrete");
+  if (p->d == 1 && p->M > 4096) return fail(GRF_ERR_UNSUPPORTED, "the adjoint is built for 1-D grids up to 8192");
   cudaStream_t s = (cudaStream_t)stream;
   const float* G = (const float*)grad_out;
   if (p->d == 1) {
@@ -683,6 +724,7 @@ grf_status grf_rfft_forward(grf_plan p, int64_t batch, const void* in, void* out
   if (!in || !out_halfspec) return fail(GRF_ERR_INVALID_ARG, "NULL pointer");
   if (batch < 1 || batch > p->max_batch) return fail(GRF_ERR_INVALID_ARG, "batch must be in [1, max_batch]");
   if (p->prec != GRF_FP32) return fail(GRF_ERR_UNSUPPORTED, "rfft is built for FP32 plans");
+  if (p->d == 1 && p->M > 4096) return fail(GRF_ERR_UNSUPPORTED, "rfft is built for 1-D grids up to 8192");
   cudaStream_t s = (cudaStream_t)stream;
   const HalfGeom g = half_geom(p, 0, 0);
   float2* H = (float2*)out_halfspec;

@@ -430,6 +430,65 @@ __global__ void __launch_bounds__(512) row_kernel(RowArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Four-step c2r for long 1-D grids
+// ---------------------------------------------------------------------------
+
+// X[k] = s_k xi_k of a 1-D field (xi real at the self-conjugate k = 0 and k = M).
+GRF_DEV float2 x1d(int k, int M, const float* __restrict__ stab, uint64_t key) {
+  return cscale(alg2_xi_1d(k, M, key), __ldg(stab + k));
+}
+
+template <int P>
+__global__ void __launch_bounds__(512) fourstep_stage1(FourStepArgs a) {
+  extern __shared__ float2 sm[];
+  const int C = a.C;
+  const int t = threadIdx.x;
+  const int c = t & (C - 1);
+  const int tau = t / C;
+  const int TPT = a.B / P;
+  const int k1 = blockIdx.x * C + c;  // < A: C divides A
+  const int64_t field = blockIdx.z;
+  const uint64_t key = a.seed + (uint64_t)(a.field0 + field);
+  float2 v[P];
+#pragma unroll
+  for (int q = 0; q < P; ++q) {
+    const int k = k1 + a.A * (tau + TPT * q);
+    const int mk = a.M - k;  // k = 0 pairs with X[M]
+    v[q] = c2r_pre(x1d(k, a.M, a.stab, key), x1d(mk, a.M, a.stab, key), __ldg(a.twN + k));
+  }
+  fft_core<P, +1>(v, sm, tau, c, C, a.B, a.logB, a.twB, a.tws);
+  float2* Y = a.Y + field * (int64_t)a.M + ((k1 >> a.logT) * (int64_t)a.B << a.logT) + (k1 & (a.T - 1));
+#pragma unroll
+  for (int q = 0; q < P; ++q) {
+    const int n2 = tau + TPT * q;
+    Y[(int64_t)n2 << a.logT] = cmul(v[q], __ldg(a.twM + n2 * k1));
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(512) fourstep_stage2(FourStepArgs a) {
+  extern __shared__ float2 sm[];
+  const int C = a.C;
+  const int t = threadIdx.x;
+  const int c = t & (C - 1);
+  const int tau = t / C;
+  const int TPT = a.A / P;
+  const int n2 = blockIdx.x * C + c;  // < B: C divides B
+  const int64_t field = blockIdx.z;
+  const float2* Y = a.Yin + field * (int64_t)a.M + ((int64_t)n2 << a.logT);
+  float2 v[P];
+#pragma unroll
+  for (int q = 0; q < P; ++q) {
+    const int k1 = tau + TPT * q;
+    v[q] = Y[((k1 >> a.logT) * (int64_t)a.B << a.logT) + (k1 & (a.T - 1))];
+  }
+  fft_core<P, +1>(v, sm, tau, c, C, a.A, a.logA, a.twA, a.tws);
+  float2* o = reinterpret_cast<float2*>(a.out + field * (int64_t)a.N);
+#pragma unroll
+  for (int q = 0; q < P; ++q) o[n2 + (int64_t)a.B * (tau + TPT * q)] = v[q];
+}
+
+// ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
 
@@ -544,6 +603,34 @@ static cudaError_t launch_row_p(int P, const RowArgs& a, dim3 grid, cudaStream_t
     case 8: return launch_row_t<8, SRC, MODE>(a, grid, s);
     case 16: return launch_row_t<16, SRC, MODE>(a, grid, s);
     default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int P>
+static cudaError_t launch_fourstep_t(int stage, const FourStepArgs& a, int64_t nfields, cudaStream_t s) {
+  const int len = stage == 1 ? a.B : a.A;
+  const int ncols = stage == 1 ? a.A : a.B;
+  const int threads = a.C * len / P;
+  const size_t smem = col_smem_bytes(len, a.C);
+  const dim3 grid((unsigned)(ncols / a.C), 1, (unsigned)nfields);
+  if (stage == 1) {
+    auto k = fourstep_stage1<P>;
+    cudaError_t e = prepare_kernel((const void*)k, threads, smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, threads, smem, s>>>(a);
+  } else {
+    auto k = fourstep_stage2<P>;
+    cudaError_t e = prepare_kernel((const void*)k, threads, smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, threads, smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fourstep(int stage, int P, const FourStepArgs& a, int64_t nfields, cudaStream_t s) {
+  switch (P) {
+    case 16: return launch_fourstep_t<16>(stage, a, nfields, s);
+    default: return cudaErrorInvalidValue;  // both factors are >= 16
   }
 }
 

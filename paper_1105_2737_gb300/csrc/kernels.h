@@ -70,6 +70,31 @@ struct RowArgs {
   double* partial;    // ROW_R2C_ADJ
 };
 
+// Four-step c2r for long 1-D grids (Algorithm 2): M = N/2 = A * B.
+//   stage 1: for every column k1 < A, the sequence Z[k1 + A k2] (k2 < B) of the
+//            c2r split, built from X[k] = s_k xi_k and X[M - k] drawn in
+//            registers, inverse FFT of length B, times exp(2 pi i n2 k1 / M);
+//            stored as Y[k1 / T][n2][k1 % T] (T = columns per CTA of stage 1).
+//   stage 2: for every n2 < B, inverse FFT of length A over k1 gives
+//            z[n2 + B n1]; f[2m] = Re z[m], f[2m + 1] = Im z[m].
+struct FourStepArgs {
+  int A, logA, B, logB, M, N;
+  int C;             // columns per CTA
+  int T, logT;       // tile of Y (the column count per CTA of stage 1)
+  float2* Y;         // one field = M complex, fields back to back
+  const float2* Yin;
+  float* out;        // N floats per field
+  const float2* twA; // exp(2 pi i k / A)
+  const float2* twB;
+  const float2* twM; // exp(2 pi i k / M), k < M
+  const float2* twN; // exp(2 pi i k / N), k < M
+  const float2* tws;
+  const float* stab; // s_k, k <= M
+  uint64_t seed;
+  int64_t field0;
+};
+cudaError_t launch_fourstep(int stage, int P, const FourStepArgs& a, int64_t nfields, cudaStream_t s);
+
 // Host launchers (fft_kernels.cu).  P is the points per thread of the
 // transform (16 if the length is >= 16, else the length itself).
 cudaError_t launch_col(int src, int mode, int P, const ColArgs& a, dim3 grid, cudaStream_t s);

@@ -93,6 +93,25 @@ def test_fields_1d(N, Lx, alg):
     _compare(f, ref)
 
 
+@pytest.mark.parametrize("N", [2 ** 14, 2 ** 16, 2 ** 17, 2 ** 20])
+def test_fields_1d_four_step(N):
+    """Long 1-D grids: c2r by the four-step decomposition M = A B."""
+    kw = dict(ell=0.01, nu=1.5)
+    batch = 3
+    g = _api().GRF((N,), (1.0,), family="matern", max_batch=batch, **kw)
+    f = g.sample(seed=8, batch=batch).cpu().numpy()
+    ref = O.sample((N,), (1.0,), _ospec("matern", **kw), seed=8, batch=batch)
+    _compare(f, ref)
+
+
+def test_fields_1d_four_step_fp64():
+    kw = dict(ell=0.01, nu=1.5)
+    g = _api().GRF((2 ** 16,), (1.0,), family="matern", precision="fp64", max_batch=2, **kw)
+    f = g.sample(seed=8, batch=2).cpu().numpy()
+    ref = O.sample((2 ** 16,), (1.0,), _ospec("matern", **kw), seed=8, batch=2)
+    assert np.linalg.norm(f - ref) / np.linalg.norm(ref) <= 1e-12
+
+
 CASES_3D = [((16, 16, 16), (1.0, 1.0, 1.0), "gaussian", dict(ell=0.1)),
             ((8, 32, 64), (1.0, 2.0, 1.0), "matern", dict(ell=0.1, nu=1.5)),
             ((32, 32, 32), (1.0, 1.0, 1.0), "gaussian", dict(ell=0.03)),
