@@ -233,6 +233,16 @@ grf_status grf_sample_2d_static(const int64_t* n, const double* L, const grf_spe
                                 int64_t batch, float* out, void* stream);
 
 /*
+ * grf_batch_set_debug - test hook of a batch plan (no counterpart in the
+ * paper).  withhold_field >= 0 makes the first pass of that field never report
+ * completion, so the tiles that depend on it wait until their bounded wait
+ * runs out: the launch then stops, returns, and grf_status_word reports
+ * GRF_ERR_TIMEOUT.  timeout_ms > 0 sets the wait limit (default 2000 ms).
+ * withhold_field = -1 restores normal operation.  Drops any captured graph.
+ */
+grf_status grf_batch_set_debug(grf_plan p, int withhold_field, double timeout_ms);
+
+/*
  * grf_status_word - synchronise `stream`, read and clear the plan's device
  * status word (GRF_OK or GRF_ERR_TIMEOUT).
  */

@@ -63,6 +63,7 @@ def lib():
             "grf_batch_sample": (C.c_int, [P, U64, C.POINTER(VP), VP]),
             "grf_batch_graph_launch": (C.c_int, [P, U64, C.POINTER(VP), VP]),
             "grf_status_word": (C.c_int, [P, VP]),
+            "grf_batch_set_debug": (C.c_int, [P, C.c_int, C.c_double]),
             "grf_philox_words": (C.c_int, [U64, C.c_uint32, U64, I64, VP, VP]),
             "grf_sample_2d_static": (C.c_int, [C.POINTER(I64), C.POINTER(D), C.POINTER(grf_spectrum), U64, I64,
                                                VP, VP]),
@@ -158,6 +159,10 @@ def grf_batch_sample(plan, seed, out_ptrs, stream=0):
 def grf_batch_graph_launch(plan, seed, out_ptrs, stream=0):
     arr = _ptr_array(out_ptrs)
     check(lib().grf_batch_graph_launch(plan, C.c_uint64(seed), arr, C.c_void_p(stream)), "grf_batch_graph_launch")
+
+
+def grf_batch_set_debug(plan, withhold_field=-1, timeout_ms=0.0):
+    check(lib().grf_batch_set_debug(plan, int(withhold_field), float(timeout_ms)), "grf_batch_set_debug")
 
 
 def grf_status_word(plan, stream=0) -> int:

@@ -171,6 +171,9 @@ class GRFBatch:
         with torch.cuda.device(self.device):
             return L.grf_status_word(self.handle, _stream_ptr(self.device))
 
+    def set_debug(self, withhold_field: int = -1, timeout_ms: float = 0.0):
+        L.grf_batch_set_debug(self.handle, withhold_field, timeout_ms)
+
     @property
     def total_points(self) -> int:
         return L.grf_plan_query(self.handle, 0)

@@ -794,6 +794,13 @@ grf_status grf_batch_graph_launch(grf_plan p, uint64_t seed, void* const* out, v
   return st == GRF_OK ? st : fail(st, err);
 }
 
+grf_status grf_batch_set_debug(grf_plan p, int withhold_field, double timeout_ms) {
+  grf_status st = check_plan(p);
+  if (st != GRF_OK) return st;
+  if (p->kind != 1) return fail(GRF_ERR_INVALID_ARG, "not a batch plan");
+  return batch_plan_debug(p->batch, withhold_field, timeout_ms);
+}
+
 grf_status grf_status_word(grf_plan p, void* stream) {
   grf_status st = check_plan(p);
   if (st != GRF_OK) return st;

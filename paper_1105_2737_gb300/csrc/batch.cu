@@ -1,25 +1,744 @@
+// Uneven batches: thousands of fields of different shapes, dimensions and
+// Matern / Gaussian parameters sampled (Algorithm 2, FP32) by ONE persistent
+// kernel launch, optionally replayed from a CUDA graph.
+//
+// Work decomposition.  Every field is a short chain of passes (2-D: noise +
+// axis-1 columns, then c2r rows; 3-D: noise + axis-1 columns, axis-2 columns,
+// c2r rows; 1-D: the two stages of the four-step c2r).  A pass is split into
+// tiles (a few columns or rows, one CTA-sized piece of work).  The queue holds
+// every (pass, tile) of every field, all first passes first, then all second
+// passes, then all third passes.  Persistent CTAs pop tiles in queue order
+// with one atomic; a tile of pass p of field f first waits until the per-field
+// counter of pass p - 1 reaches that pass's tile count.  Because tiles are
+// popped in queue order, everything a tile waits for has already been popped
+// by a running CTA, so the waits end.  Each wait is still bounded (iteration
+// cap and a %globaltimer deadline): on expiry the kernel records
+// GRF_ERR_TIMEOUT in the plan's status word, raises an abort flag that makes
+// every CTA stop taking tiles, and returns.
+//
+// Schedules: threads per tile and CTAs per SM are chosen by a tuner that
+// times the candidates on the first call and keeps the winner in a cache file
+// (GRF_TUNE_CACHE, default $HOME/.cache/grf_gb300_tune.txt) keyed by the GPU
+// name and the batch's shape signature.
 #include "batch.h"
+#include "bodies.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include <sys/stat.h>
 
 namespace grf {
+
+enum JobKind { JOB_COL_NOISE = 0, JOB_COL_LOAD = 1, JOB_ROW_C2R = 2, JOB_FS1 = 3, JOB_FS2 = 4 };
+
+struct Job {
+  int kind, pass, nthr;
+  int gx;         // tile -> (bx = tile % gx, by = tile / gx)
+  int field;      // index in the batch (seed + field is its Philox key)
+  int need_prev;  // tiles of the previous pass of this field
+  ColArgs col;
+  RowArgs row;
+  FourStepArgs fs;
+};
+
+struct BatchParams {
+  const Job* jobs;
+  const int2* items;  // (job, tile), in queue order
+  int nitems;
+  int* queue;
+  int* counters;  // 3 per field
+  int* abort_flag;
+  int* status;
+  float* const* outs;
+  uint64_t seed;
+  long long timeout_ns;
+  int withhold_field;  // test hook: this field's first pass never reports done (-1: off)
+};
+
+constexpr int kBatchThreads = 256;
+constexpr long long kDefaultTimeoutNs = 2000000000LL;  // 2 s
+constexpr unsigned kSpinCap = 1u << 26;
+
+GRF_DEV unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+GRF_DEV int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Bounded wait for counter >= need.  Returns 1 when it is, 0 on abort or timeout.
+GRF_DEV int wait_counter(const int* ctr, int need, const BatchParams& b) {
+  const unsigned long long t0 = globaltimer_ns();
+  for (unsigned it = 0;; ++it) {
+    if (ld_acquire(ctr) >= need) return 1;
+    if (ld_acquire(b.abort_flag)) return 0;
+    if (it > kSpinCap || (long long)(globaltimer_ns() - t0) > b.timeout_ns) {
+      atomicExch(b.status, (int)GRF_ERR_TIMEOUT);
+      atomicExch(b.abort_flag, 1);
+      return 0;
+    }
+    __nanosleep(256);
+  }
+}
+
+// One call per job kind, kept out of line so that each body gets its own
+// register allocation instead of the union of all five.
+__device__ __noinline__ void run_col_noise(const ColArgs& a, int bx, int by, int nthr, float2* sm) {
+  col_body<16, COL_NOISE, COL_INV>(a, bx, by, 0, 0, nthr, sm);
+}
+__device__ __noinline__ void run_col_load(const ColArgs& a, int bx, int by, int nthr, float2* sm) {
+  col_body<16, COL_LOAD, COL_INV>(a, bx, by, 0, 0, nthr, sm);
+}
+__device__ __noinline__ void run_row_c2r(const RowArgs& a, int bx, int nthr, float2* sm) {
+  row_body<16, ROW_LOAD_H, ROW_C2R>(a, bx, nthr, sm);
+}
+__device__ __noinline__ void run_fs1(const FourStepArgs& a, int bx, int nthr, float2* sm) {
+  fourstep1_body<16>(a, bx, 0, nthr, sm);
+}
+__device__ __noinline__ void run_fs2(const FourStepArgs& a, int bx, int nthr, float2* sm) {
+  fourstep2_body<16>(a, bx, 0, nthr, sm);
+}
+
+__global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(BatchParams b) {
+  extern __shared__ float2 sm[];
+  __shared__ Job s_job;
+  __shared__ int s_item, s_ok;
+  const int t = threadIdx.x;
+  for (;;) {
+    if (t == 0) {
+      const int i = atomicAdd(b.queue, 1);
+      s_item = (i < b.nitems && !ld_acquire(b.abort_flag)) ? i : -1;
+    }
+    __syncthreads();
+    const int i = s_item;
+    if (i < 0) break;
+    const int2 it = b.items[i];
+    {  // stage the job descriptor in shared memory
+      const int* src = reinterpret_cast<const int*>(b.jobs + it.x);
+      int* dst = reinterpret_cast<int*>(&s_job);
+      for (int w = t; w < (int)(sizeof(Job) / sizeof(int)); w += kBatchThreads) dst[w] = src[w];
+    }
+    __syncthreads();
+    if (t == 0) {
+      s_job.col.g.seed = b.seed;
+      s_job.row.g.seed = b.seed;
+      s_job.fs.seed = b.seed;
+      if (s_job.kind == JOB_ROW_C2R) s_job.row.outR = b.outs[s_job.field];
+      if (s_job.kind == JOB_FS2) s_job.fs.out = b.outs[s_job.field];
+      s_ok = s_job.pass == 0 ? 1 : wait_counter(b.counters + 3 * s_job.field + s_job.pass - 1, s_job.need_prev, b);
+    }
+    __syncthreads();
+    if (!s_ok) break;
+    const int bx = it.y % s_job.gx, by = it.y / s_job.gx;
+    const int nthr = s_job.nthr;
+    if (t < nthr) {
+      switch (s_job.kind) {
+        case JOB_COL_NOISE: run_col_noise(s_job.col, bx, by, nthr, sm); break;
+        case JOB_COL_LOAD: run_col_load(s_job.col, bx, by, nthr, sm); break;
+        case JOB_ROW_C2R: run_row_c2r(s_job.row, bx, nthr, sm); break;
+        case JOB_FS1: run_fs1(s_job.fs, bx, nthr, sm); break;
+        default: run_fs2(s_job.fs, bx, nthr, sm); break;
+      }
+    }
+    __syncthreads();
+    if (t == 0 && !(s_job.pass == 0 && s_job.field == b.withhold_field)) {
+      __threadfence();  // the tile's writes (ordered by the barrier) before the count
+      atomicAdd(b.counters + 3 * s_job.field + s_job.pass, 1);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+struct FieldInfo {
+  int d;
+  int n[3];
+  double L[3];
+  grf_spectrum spec;
+  int64_t points, stab_off, ws_off;
+};
 
 struct BatchPlan {
   int64_t count = 0;
   int64_t total_points = 0;
+  std::vector<FieldInfo> fields;
+  int twmax = 0;
+  float2* tw = nullptr;
+  float* stabs = nullptr;
+  float2* ws = nullptr;
+  Job* jobs = nullptr;
+  int2* items = nullptr;
+  int njobs = 0, nitems = 0;
+  int* counters = nullptr;  // 3 per field, then queue, abort flag
+  float** outs = nullptr;
+  size_t smem = 0;
+  int num_sms = 0;
+  // schedule
+  int tile_threads = 256;
+  int ctas_per_sm = 2;
+  bool tuned = false;
+  std::string signature;
+  // graph replay
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphNode_t knode = nullptr;
+  std::vector<void*> graph_outs;
+  std::vector<void*> cur_outs;
+  BatchParams kparams{};
+  int withhold = -1;
+  long long timeout_ns = kDefaultTimeoutNs;
 };
 
-grf_status batch_plan_build(BatchPlan** out, int64_t, const int*, const int64_t*, const double*,
-                            const grf_spectrum*, std::string* err) {
-  *out = nullptr;
-  *err = "uneven batches are not built yet";
-  return GRF_ERR_UNSUPPORTED;
+namespace {
+
+bool pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
+int lg2(int64_t x) {
+  int r = 0;
+  while ((int64_t(1) << r) < x) ++r;
+  return r;
+}
+int64_t npow2(int64_t x) {
+  int64_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
 }
 
-grf_status batch_plan_sample(BatchPlan*, uint64_t, void* const*, cudaStream_t, int*, bool, std::string* err) {
-  *err = "uneven batches are not built yet";
-  return GRF_ERR_UNSUPPORTED;
+// Columns (or rows) per tile for transforms of length len: `target` threads of
+// 16 points, at least one warp, no more than the columns there are.
+int tile_cols(int len, int64_t ncols, int target) {
+  const int tpt = len / 16;
+  int C = target / tpt;
+  if (C < 1) C = 1;
+  const int cmin = 32 / tpt > 1 ? 32 / tpt : 1;
+  const int64_t cp = npow2(ncols);
+  if (C > cp) C = (int)cp;
+  if (C < cmin) C = cmin;
+  return C;
+}
+
+std::string gpu_name() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp pr;
+  if (cudaGetDeviceProperties(&pr, dev) != cudaSuccess) return "unknown";
+  std::string s = pr.name;
+  for (char& c : s)
+    if (c == ' ' || c == '=' || c == '\n') c = '_';
+  return s;
+}
+
+std::string cache_path() {
+  const char* e = std::getenv("GRF_TUNE_CACHE");
+  if (e && *e) return e;
+  const char* h = std::getenv("HOME");
+  return std::string(h ? h : "/tmp") + "/.cache/grf_gb300_tune.txt";
+}
+
+std::mutex g_cache_mu;
+
+bool cache_lookup(const std::string& key, int* a, int* b) {
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  std::ifstream f(cache_path());
+  std::string line;
+  bool found = false;
+  while (std::getline(f, line)) {
+    std::istringstream is(line);
+    std::string k;
+    int x, y;
+    if (is >> k >> x >> y && k == key) {
+      *a = x;
+      *b = y;
+      found = true;  // the last entry wins
+    }
+  }
+  return found;
+}
+
+void cache_store(const std::string& key, int a, int b) {
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  const std::string path = cache_path();
+  const size_t slash = path.find_last_of('/');
+  if (slash != std::string::npos) mkdir(path.substr(0, slash).c_str(), 0755);  // best effort
+  std::ofstream f(path, std::ios::app);
+  if (f) f << key << " " << a << " " << b << "\n";
+}
+
+cudaError_t build_jobs(BatchPlan* b) {
+  std::vector<Job> jobs;
+  std::vector<int2> items[3];
+  const float2* tws = b->tw + 2 * b->twmax;
+  for (int64_t i = 0; i < b->count; ++i) {
+    const FieldInfo& f = b->fields[i];
+    const int d = f.d;
+    const int Nd = f.n[d - 1], M = Nd / 2;
+    HalfGeom g{};
+    g.d = d;
+    g.N1 = d >= 2 ? f.n[0] : 1;
+    g.Nmid = d == 3 ? f.n[1] : 1;
+    g.M = M;
+    g.Q = (uint32_t)(M / 2 + 1);
+    g.seed = 0;
+    g.field0 = i;  // key = seed + i
+    g.stab = b->stabs + f.stab_off;
+    float2* ws = b->ws + f.ws_off;
+    auto add = [&](Job j, int tiles) {
+      const int id = (int)jobs.size();
+      jobs.push_back(j);
+      for (int t = 0; t < tiles; ++t) items[j.pass].push_back(make_int2(id, t));
+      return tiles;
+    };
+    if (d == 1) {
+      const int lm = lg2(M);
+      FourStepArgs fs{};
+      fs.B = 1 << ((lm + 1) / 2);
+      fs.A = M / fs.B;
+      fs.logA = lg2(fs.A);
+      fs.logB = lg2(fs.B);
+      fs.M = M;
+      fs.N = Nd;
+      const int C1 = std::min(tile_cols(fs.B, fs.A, b->tile_threads), fs.A);
+      const int C2 = std::min(tile_cols(fs.A, fs.B, b->tile_threads), fs.B);
+      fs.T = C1;
+      fs.logT = lg2(C1);
+      fs.Y = ws;
+      fs.Yin = ws;
+      fs.twA = b->tw + fs.A;
+      fs.twB = b->tw + fs.B;
+      fs.twM = b->tw + M;
+      fs.twN = b->tw + Nd;
+      fs.tws = tws;
+      fs.stab = g.stab;
+      fs.field0 = i;
+      Job j1{};
+      j1.kind = JOB_FS1;
+      j1.pass = 0;
+      j1.field = (int)i;
+      j1.fs = fs;
+      j1.fs.C = C1;
+      j1.nthr = C1 * fs.B / 16;
+      j1.gx = fs.A / C1;
+      const int t1 = add(j1, j1.gx);
+      Job j2 = j1;
+      j2.kind = JOB_FS2;
+      j2.pass = 1;
+      j2.fs.C = C2;
+      j2.nthr = C2 * fs.A / 16;
+      j2.gx = fs.B / C2;
+      j2.need_prev = t1;
+      add(j2, j2.gx);
+      continue;
+    }
+    // 2-D and 3-D: axis-1 columns with the noise
+    ColArgs a{};
+    a.N = g.N1;
+    a.logN = lg2(g.N1);
+    a.ncols = (int64_t)g.Nmid * (M + 1);
+    a.C = tile_cols(a.N, a.ncols, b->tile_threads);
+    a.T = 1;
+    a.logT = 0;
+    a.out = ws;
+    a.tw = b->tw + g.N1;
+    a.tws = tws;
+    a.g = g;
+    Job ja{};
+    ja.kind = JOB_COL_NOISE;
+    ja.pass = 0;
+    ja.field = (int)i;
+    ja.col = a;
+    ja.nthr = a.C * a.N / 16;
+    ja.gx = (int)((a.ncols + a.C - 1) / a.C);
+    int prev = add(ja, ja.gx);
+    int pass = 1;
+    if (d == 3) {
+      ColArgs a2{};
+      a2.N = g.Nmid;
+      a2.logN = lg2(g.Nmid);
+      a2.ncols = M + 1;
+      a2.C = tile_cols(a2.N, a2.ncols, b->tile_threads);
+      a2.T = 1;
+      a2.logT = 0;
+      a2.ostride = (int64_t)g.Nmid * (M + 1);
+      a2.in = ws;
+      a2.out = ws;
+      a2.tw = b->tw + g.Nmid;
+      a2.tws = tws;
+      a2.g = g;
+      Job jb{};
+      jb.kind = JOB_COL_LOAD;
+      jb.pass = 1;
+      jb.field = (int)i;
+      jb.col = a2;
+      jb.nthr = a2.C * a2.N / 16;
+      jb.gx = (int)((a2.ncols + a2.C - 1) / a2.C);
+      jb.need_prev = prev;
+      prev = add(jb, jb.gx * g.N1);
+      pass = 2;
+    }
+    RowArgs r{};
+    r.M = M;
+    r.logM = lg2(M);
+    r.rows_per_field = (int64_t)g.N1 * g.Nmid;
+    r.nrows = r.rows_per_field;
+    r.C = tile_cols(M, r.nrows, b->tile_threads);
+    r.T = 1;
+    r.logT = 0;
+    r.inH = ws;
+    r.twM = b->tw + M;
+    r.twN = b->tw + Nd;
+    r.tws = tws;
+    r.g = g;
+    Job jr{};
+    jr.kind = JOB_ROW_C2R;
+    jr.pass = pass;
+    jr.field = (int)i;
+    jr.row = r;
+    jr.nthr = r.C * M / 16;
+    jr.gx = (int)(r.nrows / r.C);
+    jr.need_prev = prev;
+    add(jr, jr.gx);
+  }
+  std::vector<int2> all;
+  for (int p = 0; p < 3; ++p) all.insert(all.end(), items[p].begin(), items[p].end());
+  cudaFree(b->jobs);
+  cudaFree(b->items);
+  b->jobs = nullptr;
+  b->items = nullptr;
+  cudaError_t e = cudaMalloc(&b->jobs, jobs.size() * sizeof(Job));
+  if (e == cudaSuccess) e = cudaMalloc(&b->items, all.size() * sizeof(int2));
+  if (e == cudaSuccess) e = cudaMemcpy(b->jobs, jobs.data(), jobs.size() * sizeof(Job), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->items, all.data(), all.size() * sizeof(int2), cudaMemcpyHostToDevice);
+  b->njobs = (int)jobs.size();
+  b->nitems = (int)all.size();
+  size_t smem = 3 * 32 * sizeof(double);
+  for (const Job& j : jobs) {
+    size_t need = 0;
+    if (j.kind == JOB_COL_NOISE || j.kind == JOB_COL_LOAD) need = col_smem_bytes(j.col.N, j.col.C);
+    else if (j.kind == JOB_ROW_C2R) need = row_smem_bytes(j.row.M, j.row.C);
+    else need = col_smem_bytes(j.kind == JOB_FS1 ? j.fs.B : j.fs.A, j.fs.C);
+    smem = std::max(smem, need);
+  }
+  b->smem = smem;
+  return e;
+}
+
+}  // namespace
+}  // namespace grf
+
+namespace grf {
+namespace {
+
+cudaError_t launch_batch(BatchPlan* b, uint64_t seed, cudaStream_t s, int* status) {
+  cudaError_t e = cudaMemsetAsync(b->counters, 0, (size_t)(3 * b->count + 2) * sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  BatchParams p{};
+  p.jobs = b->jobs;
+  p.items = b->items;
+  p.nitems = b->nitems;
+  p.counters = b->counters;
+  p.queue = b->counters + 3 * b->count;
+  p.abort_flag = b->counters + 3 * b->count + 1;
+  p.status = status;
+  p.outs = b->outs;
+  p.seed = seed;
+  p.timeout_ns = b->timeout_ns;
+  p.withhold_field = b->withhold;
+  e = prepare_kernel((const void*)batch_kernel, kBatchThreads, b->smem);
+  if (e != cudaSuccess) return e;
+  const int grid = b->num_sms * b->ctas_per_sm;
+  batch_kernel<<<grid, kBatchThreads, b->smem, s>>>(p);
+  b->kparams = p;
+  return cudaGetLastError();
+}
+
+cudaError_t set_outs(BatchPlan* b, void* const* out, cudaStream_t s) {
+  std::vector<void*> v(out, out + b->count);
+  if (v == b->cur_outs) return cudaSuccess;
+  // pageable source: the copy is staged before the call returns, ordered on s
+  cudaError_t e = cudaMemcpyAsync(b->outs, v.data(), v.size() * sizeof(void*), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) b->cur_outs = v;
+  return e;
+}
+
+// Time one launch of the current schedule (after a warm-up launch).
+float time_launch(BatchPlan* b, uint64_t seed, cudaStream_t s, int* status) {
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  launch_batch(b, seed, s, status);
+  cudaEventRecord(e0, s);
+  launch_batch(b, seed, s, status);
+  cudaEventRecord(e1, s);
+  cudaEventSynchronize(e1);
+  float ms = 1e30f;
+  if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) ms = 1e30f;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return ms;
+}
+
+// The tuner: threads per tile x CTAs per SM, timed on the caller's outputs.
+cudaError_t tune(BatchPlan* b, uint64_t seed, cudaStream_t s, int* status) {
+  int occ = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel, kBatchThreads, b->smem);
+  if (occ < 1) occ = 1;
+  float best = 1e30f;
+  int bt = b->tile_threads, bc = b->ctas_per_sm;
+  for (int tt : {128, 256}) {
+    b->tile_threads = tt;
+    cudaError_t e = build_jobs(b);
+    if (e != cudaSuccess) return e;
+    for (int cps = 1; cps <= std::min(occ, 4); ++cps) {
+      b->ctas_per_sm = cps;
+      const float ms = time_launch(b, seed, s, status);
+      if (ms < best) {
+        best = ms;
+        bt = tt;
+        bc = cps;
+      }
+    }
+  }
+  b->tile_threads = bt;
+  b->ctas_per_sm = bc;
+  cudaError_t e = build_jobs(b);
+  if (e != cudaSuccess) return e;
+  b->tuned = true;
+  cache_store(b->signature, bt, bc);
+  return cudaSuccess;
+}
+
+void drop_graph(BatchPlan* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  b->knode = nullptr;
+  b->graph_outs.clear();
+}
+
+}  // namespace
+
+grf_status batch_plan_build(BatchPlan** out, int64_t count, const int* d, const int64_t* n, const double* L,
+                            const grf_spectrum* spec, std::string* err) {
+  *out = nullptr;
+  if (count > (1 << 24)) {
+    *err = "too many fields";
+    return GRF_ERR_INVALID_ARG;
+  }
+  BatchPlan* b = new BatchPlan();
+  b->count = count;
+  b->fields.resize(count);
+  int64_t stab_total = 0, ws_total = 0;
+  int twmax = 16;
+  std::ostringstream sig;
+  sig << gpu_name() << "|" << count;
+  uint64_t hsh = 1469598103934665603ull;
+  for (int64_t i = 0; i < count; ++i) {
+    FieldInfo& f = b->fields[i];
+    f.d = d[i];
+    if (f.d < 1 || f.d > 3) {
+      delete b;
+      *err = "field dimension must be 1, 2 or 3";
+      return GRF_ERR_INVALID_ARG;
+    }
+    f.points = 1;
+    for (int k = 0; k < 3; ++k) {
+      f.n[k] = k < f.d ? (int)n[3 * i + k] : 1;
+      f.L[k] = k < f.d ? L[3 * i + k] : 1.0;
+      if (k < f.d) {
+        if (n[3 * i + k] < 2 || (n[3 * i + k] & 1) || !(f.L[k] > 0)) {
+          delete b;
+          *err = "every N_i must be even and every L_i > 0";
+          return GRF_ERR_INVALID_ARG;
+        }
+        const bool ok = pow2(f.n[k]) && (f.d == 1 ? (f.n[k] >= 1024 && f.n[k] <= (1 << 22))
+                                                   : (f.n[k] >= 32 && f.n[k] <= 4096));
+        if (!ok) {
+          delete b;
+          *err = "batch plans take powers of two: 1-D 1024..2^22, 2-D/3-D sides 32..4096";
+          return GRF_ERR_UNSUPPORTED;
+        }
+        f.points *= f.n[k];
+        twmax = std::max(twmax, f.n[k]);
+        hsh = (hsh ^ (uint64_t)f.n[k]) * 1099511628211ull;
+      }
+    }
+    hsh = (hsh ^ (uint64_t)(f.d + 7)) * 1099511628211ull;
+    f.spec = spec[i];
+    const int M = f.n[f.d - 1] / 2;
+    const int N1 = f.d >= 2 ? f.n[0] : 1, Nmid = f.d == 3 ? f.n[1] : 1;
+    f.stab_off = stab_total;
+    stab_total += (int64_t)(N1 / 2 + 1) * (Nmid / 2 + 1) * (M + 1);
+    stab_total = (stab_total + 63) & ~int64_t(63);
+    f.ws_off = ws_total;
+    ws_total += f.d == 1 ? M : (int64_t)N1 * Nmid * (M + 1);
+    ws_total = (ws_total + 31) & ~int64_t(31);
+    b->total_points += f.points;
+  }
+  sig << "|" << std::hex << hsh;
+  b->signature = sig.str();
+  b->twmax = twmax;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaMalloc(&b->tw, (size_t)(2 * twmax + kStageTableEntries) * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc(&b->stabs, (size_t)stab_total * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&b->ws, (size_t)ws_total * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc(&b->counters, (size_t)(3 * count + 2) * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&b->outs, (size_t)count * sizeof(float*));
+  if (e == cudaSuccess) e = build_twiddles(b->tw, twmax, 0);
+  for (int64_t i = 0; i < count && e == cudaSuccess; ++i) {
+    const FieldInfo& f = b->fields[i];
+    SpecParams sp{};
+    sp.family = f.spec.family;
+    sp.sigma = f.spec.sigma;
+    sp.ell = f.spec.ell;
+    sp.nu = f.spec.nu;
+    sp.m = f.spec.m;
+    sp.k = f.spec.k;
+    sp.l = f.spec.l;
+    sp.n = f.spec.n;
+    sp.scale = 1.0;
+    sp.d = f.d;
+    for (int k = 0; k < 3; ++k) {
+      sp.L[k] = f.L[k];
+      sp.nn[k] = f.n[k];
+    }
+    e = build_stab(b->stabs + f.stab_off, nullptr, sp, 0.0, 0);
+  }
+  if (e == cudaSuccess) {
+    int tt = 0, cps = 0;
+    if (cache_lookup(b->signature, &tt, &cps) && (tt == 128 || tt == 256) && cps >= 1 && cps <= 4) {
+      b->tile_threads = tt;
+      b->ctas_per_sm = cps;
+      b->tuned = true;
+    }
+    e = build_jobs(b);
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    *err = std::string("batch plan: ") + cudaGetErrorString(e);
+    batch_plan_free(b);
+    return e == cudaErrorMemoryAllocation ? GRF_ERR_OOM : GRF_ERR_CUDA;
+  }
+  *out = b;
+  return GRF_OK;
+}
+
+grf_status batch_plan_sample(BatchPlan* b, uint64_t seed, void* const* out, cudaStream_t s, int* status,
+                             bool use_graph, std::string* err) {
+  for (int64_t i = 0; i < b->count; ++i)
+    if (!out[i]) {
+      *err = "NULL output pointer";
+      return GRF_ERR_INVALID_ARG;
+    }
+  cudaError_t e = set_outs(b, out, s);
+  if (e == cudaSuccess && !b->tuned) {
+    const char* env = std::getenv("GRF_TUNE");
+    if (!(env && env[0] == '0')) e = tune(b, seed, s, status);
+    b->tuned = true;
+  }
+  if (e != cudaSuccess) {
+    *err = std::string("batch sample: ") + cudaGetErrorString(e);
+    return GRF_ERR_CUDA;
+  }
+  if (!use_graph) {
+    e = launch_batch(b, seed, s, status);
+    if (e != cudaSuccess) {
+      *err = std::string("batch launch: ") + cudaGetErrorString(e);
+      return GRF_ERR_CUDA;
+    }
+    return GRF_OK;
+  }
+  if (!b->exec || b->graph_outs != b->cur_outs) {
+    drop_graph(b);
+    cudaStream_t cs;
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the outs copy on s is complete
+    if (e == cudaSuccess) e = prepare_kernel((const void*)batch_kernel, kBatchThreads, b->smem);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t le = launch_batch(b, seed, cs, status);
+      cudaError_t ce = cudaStreamEndCapture(cs, &b->graph);
+      e = le != cudaSuccess ? le : ce;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e == cudaSuccess) {
+      size_t nn = 0;
+      cudaGraphGetNodes(b->graph, nullptr, &nn);
+      std::vector<cudaGraphNode_t> nodes(nn);
+      cudaGraphGetNodes(b->graph, nodes.data(), &nn);
+      for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType ty;
+        if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) b->knode = nd;
+      }
+      if (!b->knode) e = cudaErrorUnknown;
+    }
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+      drop_graph(b);
+      *err = std::string("batch graph capture: ") + cudaGetErrorString(e);
+      return GRF_ERR_CUDA;
+    }
+    b->graph_outs = b->cur_outs;
+  }
+  // the seed is a kernel parameter: set it on the instantiated graph, then replay
+  BatchParams p = b->kparams;
+  p.seed = seed;
+  p.status = status;
+  p.withhold_field = b->withhold;
+  p.timeout_ns = b->timeout_ns;
+  void* args[] = {&p};
+  cudaKernelNodeParams kp{};
+  e = cudaGraphKernelNodeGetParams(b->knode, &kp);
+  if (e == cudaSuccess) {
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    e = cudaGraphExecKernelNodeSetParams(b->exec, b->knode, &kp);
+  }
+  if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, s);
+  if (e != cudaSuccess) {
+    *err = std::string("batch graph launch: ") + cudaGetErrorString(e);
+    return GRF_ERR_CUDA;
+  }
+  return GRF_OK;
+}
+
+grf_status batch_plan_debug(BatchPlan* b, int withhold_field, double timeout_ms) {
+  drop_graph(b);
+  b->withhold = withhold_field;
+  b->timeout_ns = timeout_ms > 0 ? (long long)(timeout_ms * 1e6) : kDefaultTimeoutNs;
+  return GRF_OK;
 }
 
 int64_t batch_plan_total_points(const BatchPlan* b) { return b ? b->total_points : 0; }
-void batch_plan_free(BatchPlan* b) { delete b; }
+
+void batch_plan_free(BatchPlan* b) {
+  if (!b) return;
+  drop_graph(b);
+  cudaFree(b->tw);
+  cudaFree(b->stabs);
+  cudaFree(b->ws);
+  cudaFree(b->jobs);
+  cudaFree(b->items);
+  cudaFree(b->counters);
+  cudaFree(b->outs);
+  delete b;
+}
 
 }  // namespace grf

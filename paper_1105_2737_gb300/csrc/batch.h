@@ -15,6 +15,7 @@ grf_status batch_plan_build(BatchPlan** out, int64_t count, const int* d, const 
 grf_status batch_plan_sample(BatchPlan* b, uint64_t seed, void* const* out, cudaStream_t s, int* status,
                              bool use_graph, std::string* err);
 int64_t batch_plan_total_points(const BatchPlan* b);
+grf_status batch_plan_debug(BatchPlan* b, int withhold_field, double timeout_ms);
 void batch_plan_free(BatchPlan* b);
 
 }  // namespace grf

@@ -1,0 +1,475 @@
+// Device bodies of the FP32 passes, shared by the per-pass kernels
+// (fft_kernels.cu) and the persistent uneven-batch kernel (batch.cu).  Each
+// body takes its tile coordinates and the number of threads taking part, so a
+// persistent CTA can run a tile that needs fewer threads than it has.
+//
+#pragma once
+#include "kernels.h"
+#include "fft_core.cuh"
+
+namespace grf {
+
+// ---------------------------------------------------------------------------
+// Half-spectrum helpers
+// ---------------------------------------------------------------------------
+
+// Column index of a plane of H (axis 1 is the transform axis) -> (kmid, kd).
+struct ColGeom {
+  int kmid, kd;
+};
+GRF_DEV ColGeom col_geom(int col, const HalfGeom& g) {
+  ColGeom r;
+  r.kmid = col / (g.M + 1);
+  r.kd = col - r.kmid * (g.M + 1);
+  return r;
+}
+
+// Folded table index of (k1, kmid, kd): S depends on |p_i| only; the table is
+// [kd][fmid][f1] so that lanes along axis 1 read consecutive entries.
+GRF_DEV int fold_index(int k1, int kmid, int kd, const HalfGeom& g) {
+  const int f1 = min(k1, g.N1 - k1);
+  const int fm = min(kmid, g.Nmid - kmid);
+  return (kd * (g.Nmid / 2 + 1) + fm) * (g.N1 / 2 + 1) + f1;
+}
+
+// xi_K at (k1, kmid, kd) of field `field`.
+GRF_DEV float2 xi_at(int k1, int kmid, int kd, int64_t field, const HalfGeom& g) {
+  return alg2_xi_grid(k1, kmid, kd, g.N1, g.Nmid, g.M, g.seed + (uint64_t)(g.field0 + field));
+}
+
+// Deterministic CTA sum of three doubles: warp shuffles, then warp 0 in order.
+GRF_DEV void block_sum3(double v0, double v1, double v2, double* out3, double* scratch) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v0 += __shfl_down_sync(0xffffffffu, v0, o);
+    v1 += __shfl_down_sync(0xffffffffu, v1, o);
+    v2 += __shfl_down_sync(0xffffffffu, v2, o);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    scratch[3 * w] = v0;
+    scratch[3 * w + 1] = v1;
+    scratch[3 * w + 2] = v2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0, c = 0;
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; ++i) {
+      a += scratch[3 * i];
+      b += scratch[3 * i + 1];
+      c += scratch[3 * i + 2];
+    }
+    out3[0] = a;
+    out3[1] = b;
+    out3[2] = c;
+  }
+}
+
+// Normals (z_re, z_im) of Algorithm 2 for the entries (k1 = tau + TPT q, kmid, kd)
+// of this thread.  Rows k1 = 2i and 2i + 1 share one Philox call (words 0,1 and
+// 2,3).  With TPT even they sit on threads tau and tau ^ 1 (lanes t and t ^ C):
+// each draws the call for half of its rows and passes the partner its words.
+// With TPT == 1 both rows are this thread's (q and q ^ 1).
+template <int P>
+GRF_DEV void alg2_column_normals(float2 (&v)[P], int tau, int TPT, int C, int kmid, int kd,
+                                 const HalfGeom& g, uint64_t key) {
+  if (TPT == 1) {
+#pragma unroll
+    for (int i = 0; i < P / 2; ++i) {
+      const u32x4 w = philox_call(alg2_call_index(2 * i, kmid, kd, g.Nmid, g.M), 0u, key);
+      v[2 * i] = box_muller(w.x, w.y);
+      v[2 * i + 1] = box_muller(w.z, w.w);
+    }
+  } else if (C < 32) {
+    const bool odd = (tau & 1) != 0;
+#pragma unroll
+    for (int i = 0; i < P / 2; ++i) {
+      const int qa = odd ? i + P / 2 : i;  // this lane draws the call of its row qa
+      const int k1 = tau + TPT * qa;
+      const u32x4 w = philox_call(alg2_call_index(k1, kmid, kd, g.Nmid, g.M), 0u, key);
+      const uint32_t oa = odd ? w.z : w.x, ob = odd ? w.w : w.y;
+      const uint32_t pa = odd ? w.x : w.z, pb = odd ? w.y : w.w;
+      const uint32_t ra = __shfl_xor_sync(0xffffffffu, pa, C);
+      const uint32_t rb = __shfl_xor_sync(0xffffffffu, pb, C);
+      const float2 zo = box_muller(oa, ob);  // own row qa
+      const float2 zr = box_muller(ra, rb);  // own row qb, drawn by the partner
+      v[i] = odd ? zr : zo;
+      v[i + P / 2] = odd ? zo : zr;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < P; ++q) v[q] = alg2_normals_grid(tau + TPT * q, kmid, kd, g.Nmid, g.M, key);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Column pass
+// ---------------------------------------------------------------------------
+
+template <int P, int SRC, int MODE>
+GRF_DEV void col_body(const ColArgs& a, int bx, int by, int64_t bz, int64_t blk, int nthr, float2* sm) {
+  const int C = a.C;
+  const int t = threadIdx.x;
+  const int c = t & (C - 1);
+  const int tau = t / C;
+  const int TPT = a.N / P;
+  const int col = bx * C + c;
+  const bool valid = col < a.ncols;
+  const int64_t field = bz;
+  const int64_t base = field * a.bstride + (int64_t)by * a.ostride;
+  // in-field offset of (pos, col): (pos >> logT) * (ncols << logT) + (col << logT) + (pos & (T - 1))
+  const int rowstride = a.ncols << a.logT;
+  const int colpart = col << a.logT;
+  const int tmask = a.T - 1;
+
+  ColGeom cg{0, 0};
+  if (SRC == COL_NOISE || MODE == COL_FWD_SCALE_INV || MODE == COL_FWD_ADJ) cg = col_geom(valid ? col : 0, a.g);
+
+  float2 v[P];
+  if constexpr (SRC == COL_NOISE) {
+    const HalfGeom& g = a.g;
+    const uint64_t key = g.seed + (uint64_t)(g.field0 + field);
+    // s_K of this column: the folded table row (kd, fmid) is contiguous along axis 1
+    const float* srow = g.stab + (cg.kd * (g.Nmid / 2 + 1) + min(cg.kmid, g.Nmid - cg.kmid)) * (g.N1 / 2 + 1);
+    float s[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const int k1 = tau + TPT * q;
+      s[q] = __ldg(srow + min(k1, g.N1 - k1));
+    }
+    alg2_column_normals<P>(v, tau, TPT, C, cg.kmid, cg.kd, g, key);
+    const float r2 = 0.70710678118654752440f;
+    if (cg.kd != 0 && cg.kd != g.M) {
+#pragma unroll
+      for (int q = 0; q < P; ++q) v[q] = cscale(v[q], s[q] * r2);
+    } else {
+      // planes kd in {0, M}: conjugate pairs (Eq. conj) and the self-conjugate points
+      const int nkm = (g.Nmid - cg.kmid) & (g.Nmid - 1);
+#pragma unroll
+      for (int q = 0; q < P; ++q) {
+        const int k1 = tau + TPT * q;
+        const int nk1 = (g.N1 - k1) & (g.N1 - 1);
+        const int row = k1 * g.Nmid + cg.kmid, nrow = nk1 * g.Nmid + nkm;
+        float2 xi = make_float2(v[q].x * r2, v[q].y * r2);
+        if (row == nrow) {
+          xi = make_float2(v[q].x, 0.f);
+        } else if (row < nrow) {  // the partner -K carries the pair's normals
+          const float2 z = alg2_normals_grid(nk1, nkm, cg.kd, g.Nmid, g.M, key);
+          xi = make_float2(z.x * r2, -z.y * r2);
+        }
+        v[q] = cscale(xi, s[q]);
+      }
+    }
+    if (!valid) {
+#pragma unroll
+      for (int q = 0; q < P; ++q) v[q] = make_float2(0.f, 0.f);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const int pos = tau + TPT * q;
+      v[q] = valid ? __ldcg(a.in + base + (int64_t)((pos >> a.logT) * rowstride + colpart + (pos & tmask)))
+                   : make_float2(0.f, 0.f);
+    }
+  }
+
+  if constexpr (MODE == COL_INV) {
+    fft_core<P, +1>(v, sm, tau, c, C, a.N, a.logN, a.tw, a.tws, nthr);
+  } else {
+    fft_core<P, -1>(v, sm, tau, c, C, a.N, a.logN, a.tw, a.tws, nthr);
+  }
+
+  if constexpr (MODE == COL_FWD_SCALE_INV) {
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const int k1 = tau + TPT * q;
+      const float s = valid ? __ldg(a.g.stab + fold_index(k1, cg.kmid, cg.kd, a.g)) * a.g.alg1_scale : 0.f;
+      v[q] = cscale(v[q], s);
+    }
+    fft_core<P, +1>(v, sm, tau, c, C, a.N, a.logN, a.tw, a.tws, nthr);
+  }
+
+  if constexpr (MODE == COL_FWD_ADJ) {
+    // v[q] = G^ at K = (k1, kmid, kd).  Sum w_K d_theta s_K Re(xi_K conj G^_K).
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    if (valid) {
+      const float w = (cg.kd == 0 || cg.kd == a.g.M) ? 1.f : 2.f;
+      const int hsz = (a.g.N1 / 2 + 1) * (a.g.Nmid / 2 + 1) * (a.g.M + 1);
+#pragma unroll
+      for (int q = 0; q < P; ++q) {
+        const int k1 = tau + TPT * q;
+        const int fi = fold_index(k1, cg.kmid, cg.kd, a.g);
+        const float2 xi = xi_at(k1, cg.kmid, cg.kd, field, a.g);
+        const float re = w * fmaf(xi.x, v[q].x, xi.y * v[q].y);
+        a0 = fmaf(re, __ldg(a.g.stab + fi), a0);
+        a1 = fmaf(re, __ldg(a.g.dstab + fi), a1);
+        a2 = fmaf(re, __ldg(a.g.dstab + hsz + fi), a2);
+      }
+    }
+    double* scratch = reinterpret_cast<double*>(sm);
+    block_sum3((double)a0 * a.g.inv_sigma, (double)a1, (double)a2, a.partial + 3 * blk, scratch);
+    return;
+  }
+
+  if (valid) {
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const int pos = tau + TPT * q;
+      a.out[base + (int64_t)((pos >> a.logT) * rowstride + colpart + (pos & tmask))] = v[q];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Row pass
+// ---------------------------------------------------------------------------
+
+// Offset of row g, entry 0 in a half-spectrum array with row tile T (a power of 2):
+// (g / T) * ((M + 1) T) + (g % T); entry k adds k T.
+GRF_DEV int64_t hrow_base(int64_t g, int M, int logT) {
+  return ((g >> logT) * (int64_t)(M + 1) << logT) + (g & ((1 << logT) - 1));
+}
+
+// Z[k] of the c2r split from X[k] and X[M - k] (both in shared memory).
+GRF_DEV float2 c2r_pre(float2 X, float2 Y, float2 w) {
+  // A = X + conj Y, B = X - conj Y, Z = A + i w B
+  const float2 A = make_float2(X.x + Y.x, X.y - Y.y);
+  const float2 B = make_float2(X.x - Y.x, X.y + Y.y);
+  const float2 wB = cmul(w, B);
+  return make_float2(A.x - wB.y, A.y + wB.x);
+}
+
+// X[k] of the r2c split from Zf[k] and Zf[M - k]: 1/2 (A - i conj(w) B) with
+// A = Zk + conj Zmk, B = Zk - conj Zmk, w = exp(2 pi i k / N).
+GRF_DEV float2 r2c_post(float2 Zk, float2 Zmk, float2 w) {
+  const float2 A = make_float2(Zk.x + Zmk.x, Zk.y - Zmk.y);
+  const float2 B = make_float2(Zk.x - Zmk.x, Zk.y + Zmk.y);
+  const float2 wB = cmulc(B, w);  // B * conj(w)
+  return make_float2(0.5f * (A.x + wB.y), 0.5f * (A.y - wB.x));
+}
+
+template <int P, int SRC, int MODE>
+GRF_DEV void row_body(const RowArgs& a, int64_t bx, int nthr, float2* sm) {
+  const int C = a.C;
+  const int t = threadIdx.x;
+  const int c = t & (C - 1);
+  const int tau = t / C;
+  const int M = a.M;
+  const int N = 2 * M;
+  const int TPT = M / P;
+  const int64_t g = bx * C + c;
+  const bool valid = g < a.nrows;
+  const int64_t field = valid ? g / a.rows_per_field : 0;
+  const int64_t rowf = valid ? g - field * a.rows_per_field : 0;
+  float2 v[P];
+
+  if constexpr (MODE == ROW_C2R) {
+    // Stage X[0..M] of every row of the CTA in shared memory (all loads first).
+    const int64_t hb = hrow_base(g, M, a.logT);
+    const uint64_t key = a.g.seed + (uint64_t)(a.g.field0 + field);
+    float2 xm = make_float2(0.f, 0.f);
+    if (valid) {
+      if constexpr (SRC == ROW_LOAD_H) {
+        const float2* src = a.inH + hb;
+#pragma unroll
+        for (int q = 0; q < P; ++q) v[q] = __ldcg(src + ((int64_t)(tau + TPT * q) << a.logT));
+        if (tau == 0) xm = __ldcg(src + ((int64_t)M << a.logT));
+      } else {  // ROW_NOISE_H: d = 1, one row per field
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+          const int k = tau + TPT * q;
+          v[q] = cscale(alg2_xi_1d(k, M, key), __ldg(a.g.stab + k));
+        }
+        if (tau == 0) xm = cscale(alg2_xi_1d(M, M, key), __ldg(a.g.stab + M));
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < P; ++q) v[q] = make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < P; ++q) sm[spad(tau + TPT * q) * C + c] = v[q];
+    if (tau == 0) sm[spad(M) * C + c] = xm;
+    cta_sync(nthr);
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const int k = tau + TPT * q;
+      v[q] = c2r_pre(sm[spad(k) * C + c], sm[spad(M - k) * C + c], __ldg(a.twN + k));
+    }
+    if constexpr (P < 16) cta_sync(nthr);
+    fft_core<P, +1>(v, sm, tau, c, C, M, a.logM, a.twM, a.tws, nthr);
+    if (valid) {
+      float2* o = reinterpret_cast<float2*>(a.outR + g * N);
+#pragma unroll
+      for (int q = 0; q < P; ++q) o[tau + TPT * q] = v[q];
+    }
+    return;
+  } else {
+    // Forward r2c of a real row: z[m] = x[2m] + i x[2m+1].
+    const uint64_t key = a.g.seed + (uint64_t)(a.g.field0 + field);
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const int m = tau + TPT * q;
+      float2 z = make_float2(0.f, 0.f);
+      if (valid) {
+        if constexpr (SRC == ROW_LOAD_REAL) {
+          z = reinterpret_cast<const float2*>(a.inR + g * N)[m];
+        } else {  // ROW_NOISE_REAL (Algorithm 1): flat index of the point
+          z = alg1_normal_pair((uint64_t)(rowf * N + 2 * m), key);
+        }
+      }
+      v[q] = z;
+    }
+    fft_core<P, -1>(v, sm, tau, c, C, M, a.logM, a.twM, a.tws, nthr);
+    cta_sync(nthr);
+#pragma unroll
+    for (int q = 0; q < P; ++q) sm[spad(tau + TPT * q) * C + c] = v[q];
+    cta_sync(nthr);
+    float2 X[P];
+    float2 XM = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const int k = tau + TPT * q;
+      const float2 Zmk = sm[spad((M - k) & (M - 1)) * C + c];
+      X[q] = r2c_post(v[q], Zmk, __ldg(a.twN + k));
+    }
+    if (tau == 0) XM = make_float2(v[0].x - v[0].y, 0.f);  // k = M: Re Z0 - Im Z0
+
+    if constexpr (MODE == ROW_R2C) {
+      if (valid) {
+        const int64_t hb = hrow_base(g, M, a.logT);
+#pragma unroll
+        for (int q = 0; q < P; ++q) a.outH[hb + ((int64_t)(tau + TPT * q) << a.logT)] = X[q];
+        if (tau == 0) a.outH[hb + ((int64_t)M << a.logT)] = XM;
+      }
+      return;
+    } else if constexpr (MODE == ROW_R2C_SCALE_C2R) {
+      // 1-D Algorithm 1: A = s_K DFT(z) / sqrt(N_tot), then c2r.
+      const float sc = a.g.alg1_scale;
+#pragma unroll
+      for (int q = 0; q < P; ++q) X[q] = cscale(X[q], __ldg(a.g.stab + tau + TPT * q) * sc);
+      if (tau == 0) XM = cscale(XM, __ldg(a.g.stab + M) * sc);
+      cta_sync(nthr);
+#pragma unroll
+      for (int q = 0; q < P; ++q) sm[spad(tau + TPT * q) * C + c] = X[q];
+      if (tau == 0) sm[spad(M) * C + c] = XM;
+      cta_sync(nthr);
+#pragma unroll
+      for (int q = 0; q < P; ++q) {
+        const int k = tau + TPT * q;
+        v[q] = c2r_pre(X[q], sm[spad(M - k) * C + c], __ldg(a.twN + k));
+      }
+      if constexpr (P < 16) cta_sync(nthr);
+      fft_core<P, +1>(v, sm, tau, c, C, M, a.logM, a.twM, a.tws, nthr);
+      if (valid) {
+        float2* o = reinterpret_cast<float2*>(a.outR + g * N);
+#pragma unroll
+        for (int q = 0; q < P; ++q) o[tau + TPT * q] = v[q];
+      }
+      return;
+    } else {  // ROW_R2C_ADJ: 1-D adjoint, one row per field
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+      if (valid) {
+#pragma unroll
+        for (int q = 0; q <= P; ++q) {
+          int k;
+          float2 G;
+          if (q < P) {
+            k = tau + TPT * q;
+            G = X[q];
+          } else {
+            if (tau != 0) break;
+            k = M;
+            G = XM;
+          }
+          const float w = (k == 0 || k == M) ? 1.f : 2.f;
+          const float2 xi = alg2_xi_1d(k, M, key);
+          const float re = w * fmaf(xi.x, G.x, xi.y * G.y);
+          a0 = fmaf(re, __ldg(a.g.stab + k), a0);
+          a1 = fmaf(re, __ldg(a.g.dstab + k), a1);
+          a2 = fmaf(re, __ldg(a.g.dstab + (M + 1) + k), a2);
+        }
+      }
+      // per-row deterministic sum over the TPT threads of the row
+      double* sd = reinterpret_cast<double*>(sm);
+      cta_sync(nthr);
+      sd[3 * t] = (double)a0 * a.g.inv_sigma;
+      sd[3 * t + 1] = a1;
+      sd[3 * t + 2] = a2;
+      cta_sync(nthr);
+      if (tau == 0 && valid) {
+        double s0 = 0, s1 = 0, s2 = 0;
+        for (int u = 0; u < TPT; ++u) {
+          const int tt = u * C + c;
+          s0 += sd[3 * tt];
+          s1 += sd[3 * tt + 1];
+          s2 += sd[3 * tt + 2];
+        }
+        a.partial[3 * g] = s0;
+        a.partial[3 * g + 1] = s1;
+        a.partial[3 * g + 2] = s2;
+      }
+      return;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Four-step c2r for long 1-D grids
+// ---------------------------------------------------------------------------
+
+// X[k] = s_k xi_k of a 1-D field (xi real at the self-conjugate k = 0 and k = M).
+GRF_DEV float2 x1d(int k, int M, const float* __restrict__ stab, uint64_t key) {
+  return cscale(alg2_xi_1d(k, M, key), __ldg(stab + k));
+}
+
+template <int P>
+GRF_DEV void fourstep1_body(const FourStepArgs& a, int bx, int64_t bz, int nthr, float2* sm) {
+  const int C = a.C;
+  const int t = threadIdx.x;
+  const int c = t & (C - 1);
+  const int tau = t / C;
+  const int TPT = a.B / P;
+  const int k1 = bx * C + c;  // < A: C divides A
+  const int64_t field = bz;
+  const uint64_t key = a.seed + (uint64_t)(a.field0 + field);
+  float2 v[P];
+#pragma unroll
+  for (int q = 0; q < P; ++q) {
+    const int k = k1 + a.A * (tau + TPT * q);
+    const int mk = a.M - k;  // k = 0 pairs with X[M]
+    v[q] = c2r_pre(x1d(k, a.M, a.stab, key), x1d(mk, a.M, a.stab, key), __ldg(a.twN + k));
+  }
+  fft_core<P, +1>(v, sm, tau, c, C, a.B, a.logB, a.twB, a.tws, nthr);
+  float2* Y = a.Y + field * (int64_t)a.M + ((k1 >> a.logT) * (int64_t)a.B << a.logT) + (k1 & (a.T - 1));
+#pragma unroll
+  for (int q = 0; q < P; ++q) {
+    const int n2 = tau + TPT * q;
+    Y[(int64_t)n2 << a.logT] = cmul(v[q], __ldg(a.twM + n2 * k1));
+  }
+}
+
+template <int P>
+GRF_DEV void fourstep2_body(const FourStepArgs& a, int bx, int64_t bz, int nthr, float2* sm) {
+  const int C = a.C;
+  const int t = threadIdx.x;
+  const int c = t & (C - 1);
+  const int tau = t / C;
+  const int TPT = a.A / P;
+  const int n2 = bx * C + c;  // < B: C divides B
+  const int64_t field = bz;
+  const float2* Y = a.Yin + field * (int64_t)a.M + ((int64_t)n2 << a.logT);
+  float2 v[P];
+#pragma unroll
+  for (int q = 0; q < P; ++q) {
+    const int k1 = tau + TPT * q;
+    v[q] = __ldcg(Y + ((k1 >> a.logT) * (int64_t)a.B << a.logT) + (k1 & (a.T - 1)));
+  }
+  fft_core<P, +1>(v, sm, tau, c, C, a.A, a.logA, a.twA, a.tws, nthr);
+  float2* o = reinterpret_cast<float2*>(a.out + field * (int64_t)a.N);
+#pragma unroll
+  for (int q = 0; q < P; ++q) o[n2 + (int64_t)a.B * (tau + TPT * q)] = v[q];
+}
+
+}  // namespace grf

@@ -113,6 +113,16 @@ GRF_DEV void dft_regs(float2 (&x)[NV]) {
   }
 }
 
+// Barrier over the first `nthr` threads of the CTA (all of them in the regular
+// kernels; a multiple of 32 when a persistent CTA runs a smaller work item).
+GRF_DEV void cta_sync(int nthr) {
+  if (nthr == (int)blockDim.x) {
+    __syncthreads();
+  } else {
+    asm volatile("bar.sync 1, %0;" ::"r"(nthr) : "memory");
+  }
+}
+
 // Padded shared-memory position.
 GRF_DEV int spad(int p) { return p + (p >> 4); }
 __host__ __device__ inline int spad_h(int p) { return p + (p >> 4); }
@@ -145,11 +155,12 @@ GRF_DEV void last_small_stage(float2 (&v)[P], int tau, int TPT, const float2* __
 //   tws : radix-16 stage tables: for the stage of span Ns (16, then 256) the
 //         entries (r - 1) Ns + m = exp(+2 pi i m r / (16 Ns)), r = 1..15, m < Ns,
 //         so that the lanes of a warp (consecutive m) read consecutive entries
-// Every exchange starts with a __syncthreads(), so the caller may have used
-// `sm` just before; after return other threads may still read `sm`.
+//   nthr: threads taking part (C * N / P), the barrier count of every exchange
+// Every exchange starts with a barrier, so the caller may have used `sm` just
+// before; after return other threads may still read `sm`.
 template <int P, int DIR>
 GRF_DEV void fft_core(float2 (&v)[P], float2* sm, int tau, int c, int C, int N, int logN,
-                      const float2* __restrict__ tw, const float2* __restrict__ tws) {
+                      const float2* __restrict__ tw, const float2* __restrict__ tws, int nthr) {
   if constexpr (P == 1) {
     return;
   } else if constexpr (P < 16) {
@@ -184,10 +195,10 @@ GRF_DEV void fft_core(float2 (&v)[P], float2* sm, int tau, int c, int C, int N, 
         const int base = (tau - m) * 16 + m;
         const int wr0 = spad(base) * C + c;
         const int wrr = (Ns + (Ns >> 4)) * C;
-        __syncthreads();
+        cta_sync(nthr);
 #pragma unroll
         for (int r = 0; r < 16; ++r) sm[wr0 + r * wrr] = v[r];
-        __syncthreads();
+        cta_sync(nthr);
         if (TPT >= 16) {
 #pragma unroll
           for (int q = 0; q < 16; ++q) v[q] = sm[rd0 + q * rdq];

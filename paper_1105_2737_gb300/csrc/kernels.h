@@ -100,6 +100,8 @@ cudaError_t launch_fourstep(int stage, int P, const FourStepArgs& a, int64_t nfi
 cudaError_t launch_col(int src, int mode, int P, const ColArgs& a, dim3 grid, cudaStream_t s);
 cudaError_t launch_row(int src, int mode, int P, const RowArgs& a, dim3 grid, cudaStream_t s);
 size_t col_smem_bytes(int N, int C);
+// Dynamic shared memory and the L1/shared carveout of a kernel for a launch shape.
+cudaError_t prepare_kernel(const void* k, int threads, size_t smem);
 size_t row_smem_bytes(int M, int C);
 int points_per_thread(int n);
 
