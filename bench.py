@@ -250,6 +250,17 @@ def run_ours(args):
         g.sample_host(seed=seed0 + i * BATCH, batch=BATCH, out=host)
     e2e_s = time.perf_counter() - t0
     e2e_val = BATCH * e_steps / e2e_s
+    # other host-delivery variants, for comparison: kernels writing pinned host
+    # memory directly over NVLink-C2C, and the staged copy over 1 and 4 streams
+    e2e_var = {}
+    for name, env in [("direct_c2c", ("GRF_HOST_DIRECT", "1")), ("copy_streams_2", ("GRF_COPY_STREAMS", "2"))]:
+        os.environ[env[0]] = env[1]
+        g.sample_host(seed=seed0, batch=BATCH, out=host)
+        t0 = time.perf_counter()
+        for i in range(e_steps):
+            g.sample_host(seed=seed0 + i * BATCH, batch=BATCH, out=host)
+        e2e_var[name] = BATCH * e_steps / (time.perf_counter() - t0)
+        del os.environ[env[0]]
     if ws > 1:
         t = torch.tensor([e2e_s], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -292,6 +303,28 @@ def run_ours(args):
     g3.close()
     del o3
 
+    # uneven batch: 4096 fields (60 % 2-D, 30 % 1-D, 10 % 3-D) in one persistent launch
+    from paper_1105_2737_gb300.api import GRFBatch
+    from paper_1105_2737_gb300.inputs import uneven_batch
+    ushapes, ulengths, uspecs = uneven_batch(4096, seed=0)
+    ub = GRFBatch(ushapes, ulengths, uspecs)
+    uouts = ub.empty()
+    ub.sample(seed=0, outs=uouts)  # first call tunes
+    ub.sample(seed=0, outs=uouts, graph=True)
+    torch.cuda.synchronize()
+    ku = max(3, min(args.steps, 20))
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    for i in range(ku):
+        ub.sample(seed=i * 4096, outs=uouts, graph=True)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    ms_u = c0.elapsed_time(c1) / ku
+    upoints = ub.total_points
+    ustatus = ub.status()
+    ub.close()
+    del uouts
+
     if rank != 0:
         return
     cpu_val, cpu_s, cores = _oracle_fields_per_s(1) if not args.no_cpu else (None, None, None)
@@ -311,9 +344,13 @@ def run_ours(args):
         "fp64_plain": {"fields_per_s": fp64_fields_per_s, "ratio_fp32_batched_over_fp64_plain": value / ws / fp64_fields_per_s},
         "extra_3d_256cubed_batch8": {"fields_per_s": fields3, "gpts_per_s": fields3 * 256 ** 3 / 1e9,
                                      "ms_per_call": ms3},
+        "extra_uneven_batch_4096": {"fields_per_s": 4096 / (ms_u / 1000.0), "gpts_per_s": upoints / (ms_u / 1e3) / 1e9,
+                                    "ms_per_launch": ms_u, "points": upoints, "status": ustatus,
+                                    "launch": "one persistent kernel per batch, CUDA graph replay"},
         "e2e": {"value": e2e_val, "unit": "fields/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": BATCH * ntot * 4,
-                "note": "grf_sample_host: seeds passed by value (no input buffers); the 64 fields are copied to pinned host memory, copies overlapped with compute"},
+                "variants_fields_per_s": e2e_var,
+                "note": "grf_sample_host into pinned host memory: device buffers, copies overlapped with compute (bounded by the ~190 GB/s device-to-host rate); seeds passed by value, no input buffers"},
         "gpu_launches": nrec,
         "clocks": clocks,
         "cpu_baseline": ({"value": cpu_val, "unit": "fields/s", "cores": cores, "kind": "oracle",

@@ -140,10 +140,13 @@ grf_status grf_sample(grf_plan p, uint64_t seed, int64_t batch, void* out, void*
 
 /*
  * grf_sample_host - same fields as grf_sample, delivered to host memory.
- *   host_out : host pointer (ideally pinned) to batch fields.
+ *   host_out : host pointer to batch fields.
  * The device computes into plan-owned buffers in chunks while earlier chunks
- * are copied out, so copies overlap compute.  Returns after the copies are
- * complete (synchronises `stream`).
+ * are copied out (each chunk over GRF_COPY_STREAMS copy streams, default 1),
+ * so copies overlap compute.  With GRF_HOST_DIRECT=1 and pinned host memory
+ * mapped into the device's address space, the kernels write the fields there
+ * directly instead.  Returns after the fields are in host memory
+ * (synchronises `stream`).
  */
 grf_status grf_sample_host(grf_plan p, uint64_t seed, int64_t batch, void* host_out, void* stream);
 

@@ -8,6 +8,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -135,7 +136,10 @@ struct grf_plan_s {
   double2* bufB = nullptr;
 
   // host delivery
+  static constexpr int kCopyStreams = 4;
   cudaStream_t copy_stream = nullptr;
+  cudaStream_t copy_streams[kCopyStreams] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev_part[2][kCopyStreams] = {};
   cudaEvent_t ev_done[2] = {nullptr, nullptr};
   cudaEvent_t ev_copied[2] = {nullptr, nullptr};
   void* stage[2] = {nullptr, nullptr};
@@ -170,6 +174,11 @@ void free_plan(grf_plan p) {
     if (p->ev_copied[i]) cudaEventDestroy(p->ev_copied[i]);
   }
   if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+  for (int i = 0; i < grf_plan_s::kCopyStreams; ++i) {
+    if (p->copy_streams[i]) cudaStreamDestroy(p->copy_streams[i]);
+    for (int j = 0; j < 2; ++j)
+      if (p->ev_part[j][i]) cudaEventDestroy(p->ev_part[j][i]);
+  }
   cudaFree(p->status);
   if (p->batch) batch_plan_free(p->batch);
   for (cudaEvent_t e : p->tev) cudaEventDestroy(e);
@@ -622,6 +631,20 @@ grf_status grf_sample_host(grf_plan p, uint64_t seed, int64_t batch, void* host_
   if (!host_out) return fail(GRF_ERR_INVALID_ARG, "host_out is NULL");
   if (batch < 1 || batch > p->max_batch) return fail(GRF_ERR_INVALID_ARG, "batch must be in [1, max_batch]");
   cudaStream_t s = (cudaStream_t)stream;
+  // Opt-in (GRF_HOST_DIRECT=1): pinned host memory that is mapped into the
+  // device's address space is written by the kernels directly (on
+  // Grace-Blackwell over NVLink-C2C).  Measured slower than the staged copies
+  // below on GB300, so it is not the default.
+  cudaPointerAttributes attr;
+  const char* direct = std::getenv("GRF_HOST_DIRECT");
+  if (direct && direct[0] == '1' && cudaPointerGetAttributes(&attr, host_out) == cudaSuccess &&
+      attr.type == cudaMemoryTypeHost && attr.devicePointer != nullptr) {
+    st = grf_sample(p, seed, batch, attr.devicePointer, stream);
+    if (st != GRF_OK) return st;
+    GRF_CUDA(cudaStreamSynchronize(s), "host delivery sync");
+    return GRF_OK;
+  }
+  cudaGetLastError();  // clear a failed attribute query on unregistered memory
   const size_t esz = p->prec == GRF_FP64 ? sizeof(double) : sizeof(float);
   const size_t field_bytes = (size_t)p->ntot * esz;
   int64_t per = (int64_t)((64u << 20) / field_bytes);
@@ -643,7 +666,15 @@ grf_status grf_sample_host(grf_plan p, uint64_t seed, int64_t batch, void* host_
       GRF_CUDA(cudaEventCreateWithFlags(&p->ev_done[i], cudaEventDisableTiming), "event");
       GRF_CUDA(cudaEventCreateWithFlags(&p->ev_copied[i], cudaEventDisableTiming), "event");
     }
+    for (int i = 0; i < grf_plan_s::kCopyStreams; ++i) {
+      GRF_CUDA(cudaStreamCreateWithFlags(&p->copy_streams[i], cudaStreamNonBlocking), "copy stream");
+      for (int j = 0; j < 2; ++j) GRF_CUDA(cudaEventCreateWithFlags(&p->ev_part[j][i], cudaEventDisableTiming), "event");
+    }
   }
+  // each chunk's copy is split over several copy streams (several copy engines)
+  const char* ncs_env = std::getenv("GRF_COPY_STREAMS");
+  int ncs = ncs_env ? std::atoi(ncs_env) : 1;
+  ncs = ncs < 1 ? 1 : (ncs > grf_plan_s::kCopyStreams ? grf_plan_s::kCopyStreams : ncs);
   int64_t idx = 0;
   for (int64_t f0 = 0; f0 < batch; f0 += per, ++idx) {
     const int64_t nb = batch - f0 < per ? batch - f0 : per;
@@ -662,10 +693,19 @@ grf_status grf_sample_host(grf_plan p, uint64_t seed, int64_t batch, void* host_
       if (st != GRF_OK) return st;
     }
     GRF_CUDA(cudaEventRecord(p->ev_done[slot], s), "record");
-    GRF_CUDA(cudaStreamWaitEvent(p->copy_stream, p->ev_done[slot], 0), "wait compute");
-    GRF_CUDA(cudaMemcpyAsync((char*)host_out + (size_t)f0 * field_bytes, p->stage[slot], nb * field_bytes,
-                             cudaMemcpyDeviceToHost, p->copy_stream),
-             "copy to host");
+    const size_t bytes = nb * field_bytes;
+    const size_t part = ((bytes + ncs - 1) / ncs + 255) & ~size_t(255);
+    for (int c = 0; c < ncs; ++c) {
+      const size_t off = (size_t)c * part;
+      if (off >= bytes) break;
+      const size_t len = bytes - off < part ? bytes - off : part;
+      GRF_CUDA(cudaStreamWaitEvent(p->copy_streams[c], p->ev_done[slot], 0), "wait compute");
+      GRF_CUDA(cudaMemcpyAsync((char*)host_out + (size_t)f0 * field_bytes + off, (char*)p->stage[slot] + off, len,
+                               cudaMemcpyDeviceToHost, p->copy_streams[c]),
+               "copy to host");
+      GRF_CUDA(cudaEventRecord(p->ev_part[slot][c], p->copy_streams[c]), "record");
+      GRF_CUDA(cudaStreamWaitEvent(p->copy_stream, p->ev_part[slot][c], 0), "join copies");
+    }
     GRF_CUDA(cudaEventRecord(p->ev_copied[slot], p->copy_stream), "record");
   }
   GRF_CUDA(cudaStreamSynchronize(p->copy_stream), "copy sync");
