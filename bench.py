@@ -173,11 +173,13 @@ def run_ours(args):
     ntot = SHAPE[0] * SHAPE[1]
     hsize = SHAPE[0] * (SHAPE[1] // 2 + 1)
     out = g.empty(BATCH)
-    seed0 = rank * 1_000_000
+    from paper_1105_2737_gb300.shard import max_over_ranks, rank_seed
+    # step i draws global fields i*B*N .. (i+1)*B*N - 1; this rank takes its contiguous share
+    seed0 = rank_seed(0, rank, ws, BATCH * ws)
     stream = torch.cuda.current_stream()
 
     def step(i):
-        g.sample(seed=seed0 + i * BATCH, batch=BATCH, out=out)
+        g.sample(seed=rank_seed(i * BATCH * ws, rank, ws, BATCH * ws), batch=BATCH, out=out)
 
     clk = ClockSampler(local).__enter__()  # sampling starts with the warm-up (GPU under load)
     for i in range(args.warmup):
@@ -201,10 +203,7 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     nrec, recs = L.grf_plan_timing_read(g.handle)
     L.grf_plan_timing(g.handle, 0)
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, device="cuda")
     fields = BATCH * args.steps * ws
     value = fields / (ms / 1000.0)
 
@@ -262,9 +261,7 @@ def run_ours(args):
         e2e_var[name] = BATCH * e_steps / (time.perf_counter() - t0)
         del os.environ[env[0]]
     if ws > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_val = BATCH * e_steps * ws / float(t.item())
+        e2e_val = BATCH * e_steps * ws / max_over_ranks(e2e_s, device="cuda")
     del host
 
     # plain FP64 form on the same GPU, one field per launch sequence
