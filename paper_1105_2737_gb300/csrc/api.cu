@@ -6,6 +6,7 @@
 #include "plain64.h"
 #include "batch.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -128,6 +129,13 @@ struct grf_plan_s {
   RowSched row;
   // four-step 1-D (M > 4096): M = A * B
   int fsA = 0, fsB = 0, fsC1 = 1, fsC2 = 1;
+  // 2-D / 3-D pipelining: the batch in `pipe` chunks, first passes on the
+  // caller's stream, the others on tail_stream
+  int pipe = 1;
+  int gs_ctas = 1;  // grid-stride CTAs per SM of each pass when pipelined (0: full grids)
+  int num_sms = 0;
+  cudaStream_t tail_stream = nullptr;
+  cudaEvent_t pipe_ev[9] = {};
 
   // FP64 plain form
   double2* tw64 = nullptr;
@@ -174,6 +182,9 @@ void free_plan(grf_plan p) {
     if (p->ev_copied[i]) cudaEventDestroy(p->ev_copied[i]);
   }
   if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+  if (p->tail_stream) cudaStreamDestroy(p->tail_stream);
+  for (cudaEvent_t e : p->pipe_ev)
+    if (e) cudaEventDestroy(e);
   for (int i = 0; i < grf_plan_s::kCopyStreams; ++i) {
     if (p->copy_streams[i]) cudaStreamDestroy(p->copy_streams[i]);
     for (int j = 0; j < 2; ++j)
@@ -280,6 +291,7 @@ HalfGeom half_geom(const grf_plan_s* p, uint64_t seed, int64_t field0) {
   g.stab = p->stab;
   g.dstab = p->dstab;
   g.inv_sigma = (float)(1.0 / p->spec.sigma);
+  g.trig = p->tw + 256;
   g.alg1_scale = (float)(1.0 / std::sqrt((double)p->ntot));
   return g;
 }
@@ -367,9 +379,15 @@ dim3 row_grid(const RowArgs& r) { return dim3((unsigned)((r.nrows + r.C - 1) / r
     if (p->tcap > 0) ++p->tused;                                                     \
   } while (0)
 
-// FP32 sampling of fields [f0, f0 + nb) into out (already offset to field f0).
-grf_status sample_chunk_fp32(grf_plan p, uint64_t seed, int64_t f0, int64_t nb, float* out, cudaStream_t s) {
+// FP32 sampling of fields [f0, f0 + nb) into out (already offset to field f0),
+// through the half-spectrum workspace `ws` (nb fields).  In 2-D and 3-D the
+// first pass (noise + axis 1) runs on `s` and the remaining passes on `st`,
+// which waits for it: with st != s, the first pass of the next chunk overlaps
+// the last passes of this one.
+grf_status sample_chunk_fp32(grf_plan p, uint64_t seed, int64_t f0, int64_t nb, float* out, cudaStream_t s,
+                             float2* ws = nullptr, cudaStream_t st = nullptr, cudaEvent_t ev = nullptr) {
   const HalfGeom g = half_geom(p, seed, f0);
+  if (!ws) ws = p->ws;
   if (p->d == 1 && p->M > 4096) {
     FourStepArgs f{};
     f.A = p->fsA;
@@ -389,6 +407,7 @@ grf_status sample_chunk_fp32(grf_plan p, uint64_t seed, int64_t f0, int64_t nb, 
     f.twN = twp(p, 2 * p->M);
     f.tws = p->tw + 2 * p->twmax;
     f.stab = p->stab;
+    f.trig = p->tw + 256;
     f.seed = seed;
     f.field0 = f0;
     f.C = p->fsC1;
@@ -405,28 +424,43 @@ grf_status sample_chunk_fp32(grf_plan p, uint64_t seed, int64_t f0, int64_t nb, 
     return GRF_OK;
   }
   const int T = p->d == 2 ? p->T : 1;
+  const bool gs = st && st != s && p->gs_ctas > 0;
   if (p->alg == 2) {
-    ColArgs a = col_axis1(p, g, nullptr, p->ws, T);
-    TLAUNCH(GRF_KERNEL_NOISE_COLUMNS, launch_col(COL_NOISE, COL_INV, p->colA.P, a, col_grid(a, 1, nb), s), "noise + axis-1 pass");
+    ColArgs a = col_axis1(p, g, nullptr, ws, T);
+    if (gs)
+      TLAUNCH(GRF_KERNEL_NOISE_COLUMNS, launch_col_noise_gs(p->colA.P, a, col_grid(a, 1, nb), p->gs_ctas * p->num_sms, s),
+              "noise + axis-1 pass");
+    else
+      TLAUNCH(GRF_KERNEL_NOISE_COLUMNS, launch_col(COL_NOISE, COL_INV, p->colA.P, a, col_grid(a, 1, nb), s),
+              "noise + axis-1 pass");
   } else {
     RowArgs r = row_args(p, g, nb, T);
-    r.outH = p->ws;
+    r.outH = ws;
     TLAUNCH(GRF_KERNEL_ROWS_R2C, launch_row(ROW_NOISE_REAL, ROW_R2C, p->row.P, r, row_grid(r), s), "alg1 noise + r2c");
     if (p->d == 3) {
-      ColArgs b = col_axis2(p, g, p->ws, p->ws);
+      ColArgs b = col_axis2(p, g, ws, ws);
       TLAUNCH(GRF_KERNEL_COLUMNS, launch_col(COL_LOAD, COL_FWD, p->colB.P, b, col_grid(b, p->N1, nb), s), "alg1 axis-2 forward");
     }
-    ColArgs a = col_axis1(p, g, p->ws, p->ws, T);
+    ColArgs a = col_axis1(p, g, ws, ws, T);
     TLAUNCH(GRF_KERNEL_COLUMNS, launch_col(COL_LOAD, COL_FWD_SCALE_INV, p->colA.P, a, col_grid(a, 1, nb), s), "alg1 axis-1 scale");
   }
+  if (st && st != s) {
+    GRF_CUDA(cudaEventRecord(ev, s), "pipeline event");
+    GRF_CUDA(cudaStreamWaitEvent(st, ev, 0), "pipeline wait");
+    s = st;
+  }
   if (p->d == 3) {
-    ColArgs b = col_axis2(p, g, p->ws, p->ws);
+    ColArgs b = col_axis2(p, g, ws, ws);
     TLAUNCH(GRF_KERNEL_COLUMNS, launch_col(COL_LOAD, COL_INV, p->colB.P, b, col_grid(b, p->N1, nb), s), "axis-2 inverse");
   }
   RowArgs r = row_args(p, g, nb, T);
-  r.inH = p->ws;
+  r.inH = ws;
   r.outR = out;
-  TLAUNCH(GRF_KERNEL_ROWS_C2R, launch_row(ROW_LOAD_H, ROW_C2R, p->row.P, r, row_grid(r), s), "c2r pass");
+  if (gs)
+    TLAUNCH(GRF_KERNEL_ROWS_C2R, launch_row_c2r_gs(p->row.P, r, row_grid(r).x, p->gs_ctas * p->num_sms, s),
+            "c2r pass");
+  else
+    TLAUNCH(GRF_KERNEL_ROWS_C2R, launch_row(ROW_LOAD_H, ROW_C2R, p->row.P, r, row_grid(r), s), "c2r pass");
   return GRF_OK;
 }
 
@@ -506,7 +540,7 @@ grf_status grf_plan_create(grf_plan* out, int d, const int64_t* n, const double*
     p->norm_scale = spec->sigma * spec->sigma / tot;
   }
 
-  int64_t maxlen = 2;
+  int64_t maxlen = 256;  // the length-256 table also serves Box-Muller's coarse angles
   for (int i = 0; i < d; ++i) maxlen = maxlen > n[i] ? maxlen : n[i];
   p->twmax = (int)maxlen;
   cudaStream_t s = nullptr;
@@ -559,6 +593,9 @@ grf_status grf_plan_create(grf_plan* out, int d, const int64_t* n, const double*
       }
       p->chunk = max_batch;
       PLAN_CUDA(dmalloc(&p->ws, (size_t)(p->chunk * p->hsize)), "workspace");
+      if (const char* pe = std::getenv("GRF_PIPELINE")) p->pipe = std::max(1, std::min(8, std::atoi(pe)));
+      if (const char* ge = std::getenv("GRF_GS_CTAS")) p->gs_ctas = std::max(0, std::min(8, std::atoi(ge)));
+      cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
     }
   } else {
     PLAN_CUDA(dmalloc(&p->tw64, 2 * maxlen), "FP64 twiddle table");
@@ -613,6 +650,28 @@ grf_status grf_sample(grf_plan p, uint64_t seed, int64_t batch, void* out, void*
                             (double*)out + b * p->ntot, s),
               "FP64 plain field");
     }
+    return GRF_OK;
+  }
+  if (p->d >= 2 && p->pipe > 1 && batch > 1) {
+    // pipeline: chunk k's noise + axis-1 pass (ALU-bound) on s overlaps chunk
+    // k-1's c2r pass (memory-bound) on the tail stream
+    if (!p->tail_stream) {
+      GRF_CUDA(cudaStreamCreateWithFlags(&p->tail_stream, cudaStreamNonBlocking), "tail stream");
+      for (cudaEvent_t& e : p->pipe_ev) GRF_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+    }
+    const int K = (int)(batch < p->pipe ? batch : p->pipe);
+    const int64_t per = (batch + K - 1) / K;
+    GRF_CUDA(cudaEventRecord(p->pipe_ev[8], s), "pipeline fork");
+    GRF_CUDA(cudaStreamWaitEvent(p->tail_stream, p->pipe_ev[8], 0), "pipeline fork");
+    int k = 0;
+    for (int64_t f0 = 0; f0 < batch; f0 += per, ++k) {
+      const int64_t nb = batch - f0 < per ? batch - f0 : per;
+      st = sample_chunk_fp32(p, seed, f0, nb, (float*)out + f0 * p->ntot, s, p->ws + f0 * p->hsize, p->tail_stream,
+                             p->pipe_ev[k % 8]);
+      if (st != GRF_OK) return st;
+    }
+    GRF_CUDA(cudaEventRecord(p->pipe_ev[8], p->tail_stream), "pipeline join");
+    GRF_CUDA(cudaStreamWaitEvent(s, p->pipe_ev[8], 0), "pipeline join");
     return GRF_OK;
   }
   const int64_t chunk = (p->d == 1 && p->M <= 4096) ? batch : p->chunk;

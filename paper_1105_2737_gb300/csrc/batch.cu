@@ -296,6 +296,7 @@ cudaError_t build_jobs(BatchPlan* b) {
     g.seed = 0;
     g.field0 = i;  // key = seed + i
     g.stab = b->stabs + f.stab_off;
+    g.trig = b->tw + 256;
     float2* ws = b->ws + f.ws_off;
     auto add = [&](Job j, int tiles) {
       const int id = (int)jobs.size();
@@ -324,6 +325,7 @@ cudaError_t build_jobs(BatchPlan* b) {
       fs.twN = b->tw + Nd;
       fs.tws = tws;
       fs.stab = g.stab;
+      fs.trig = g.trig;
       fs.field0 = i;
       Job j1{};
       j1.kind = JOB_FS1;
@@ -544,7 +546,7 @@ grf_status batch_plan_build(BatchPlan** out, int64_t count, const int* d, const 
   b->count = count;
   b->fields.resize(count);
   int64_t stab_total = 0, ws_total = 0;
-  int twmax = 16;
+  int twmax = 256;  // the length-256 table also serves Box-Muller's coarse angles
   std::ostringstream sig;
   sig << gpu_name() << "|" << count;
   uint64_t hsh = 1469598103934665603ull;

@@ -34,7 +34,7 @@ GRF_DEV int fold_index(int k1, int kmid, int kd, const HalfGeom& g) {
 
 // xi_K at (k1, kmid, kd) of field `field`.
 GRF_DEV float2 xi_at(int k1, int kmid, int kd, int64_t field, const HalfGeom& g) {
-  return alg2_xi_grid(k1, kmid, kd, g.N1, g.Nmid, g.M, g.seed + (uint64_t)(g.field0 + field));
+  return alg2_xi_grid(k1, kmid, kd, g.N1, g.Nmid, g.M, g.seed + (uint64_t)(g.field0 + field), g.trig);
 }
 
 // Deterministic CTA sum of three doubles: warp shuffles, then warp 0 in order.
@@ -79,8 +79,8 @@ GRF_DEV void alg2_column_normals(float2 (&v)[P], int tau, int TPT, int C, int km
 #pragma unroll
     for (int i = 0; i < P / 2; ++i) {
       const u32x4 w = philox_call(alg2_call_index(2 * i, kmid, kd, g.Nmid, g.M), 0u, key);
-      v[2 * i] = box_muller(w.x, w.y);
-      v[2 * i + 1] = box_muller(w.z, w.w);
+      v[2 * i] = box_muller(w.x, w.y, g.trig);
+      v[2 * i + 1] = box_muller(w.z, w.w, g.trig);
     }
   } else if (C < 32) {
     const bool odd = (tau & 1) != 0;
@@ -93,14 +93,14 @@ GRF_DEV void alg2_column_normals(float2 (&v)[P], int tau, int TPT, int C, int km
       const uint32_t pa = odd ? w.x : w.z, pb = odd ? w.y : w.w;
       const uint32_t ra = __shfl_xor_sync(0xffffffffu, pa, C);
       const uint32_t rb = __shfl_xor_sync(0xffffffffu, pb, C);
-      const float2 zo = box_muller(oa, ob);  // own row qa
-      const float2 zr = box_muller(ra, rb);  // own row qb, drawn by the partner
+      const float2 zo = box_muller(oa, ob, g.trig);  // own row qa
+      const float2 zr = box_muller(ra, rb, g.trig);  // own row qb, drawn by the partner
       v[i] = odd ? zr : zo;
       v[i + P / 2] = odd ? zo : zr;
     }
   } else {
 #pragma unroll
-    for (int q = 0; q < P; ++q) v[q] = alg2_normals_grid(tau + TPT * q, kmid, kd, g.Nmid, g.M, key);
+    for (int q = 0; q < P; ++q) v[q] = alg2_normals_grid(tau + TPT * q, kmid, kd, g.Nmid, g.M, key, g.trig);
   }
 }
 
@@ -156,7 +156,7 @@ GRF_DEV void col_body(const ColArgs& a, int bx, int by, int64_t bz, int64_t blk,
         if (row == nrow) {
           xi = make_float2(v[q].x, 0.f);
         } else if (row < nrow) {  // the partner -K carries the pair's normals
-          const float2 z = alg2_normals_grid(nk1, nkm, cg.kd, g.Nmid, g.M, key);
+          const float2 z = alg2_normals_grid(nk1, nkm, cg.kd, g.Nmid, g.M, key, g.trig);
           xi = make_float2(z.x * r2, -z.y * r2);
         }
         v[q] = cscale(xi, s[q]);
@@ -280,9 +280,9 @@ GRF_DEV void row_body(const RowArgs& a, int64_t bx, int nthr, float2* sm) {
 #pragma unroll
         for (int q = 0; q < P; ++q) {
           const int k = tau + TPT * q;
-          v[q] = cscale(alg2_xi_1d(k, M, key), __ldg(a.g.stab + k));
+          v[q] = cscale(alg2_xi_1d(k, M, key, a.g.trig), __ldg(a.g.stab + k));
         }
-        if (tau == 0) xm = cscale(alg2_xi_1d(M, M, key), __ldg(a.g.stab + M));
+        if (tau == 0) xm = cscale(alg2_xi_1d(M, M, key, a.g.trig), __ldg(a.g.stab + M));
       }
     } else {
 #pragma unroll
@@ -316,7 +316,7 @@ GRF_DEV void row_body(const RowArgs& a, int64_t bx, int nthr, float2* sm) {
         if constexpr (SRC == ROW_LOAD_REAL) {
           z = reinterpret_cast<const float2*>(a.inR + g * N)[m];
         } else {  // ROW_NOISE_REAL (Algorithm 1): flat index of the point
-          z = alg1_normal_pair((uint64_t)(rowf * N + 2 * m), key);
+          z = alg1_normal_pair((uint64_t)(rowf * N + 2 * m), key, a.g.trig);
         }
       }
       v[q] = z;
@@ -384,7 +384,7 @@ GRF_DEV void row_body(const RowArgs& a, int64_t bx, int nthr, float2* sm) {
             G = XM;
           }
           const float w = (k == 0 || k == M) ? 1.f : 2.f;
-          const float2 xi = alg2_xi_1d(k, M, key);
+          const float2 xi = alg2_xi_1d(k, M, key, a.g.trig);
           const float re = w * fmaf(xi.x, G.x, xi.y * G.y);
           a0 = fmaf(re, __ldg(a.g.stab + k), a0);
           a1 = fmaf(re, __ldg(a.g.dstab + k), a1);
@@ -420,8 +420,8 @@ GRF_DEV void row_body(const RowArgs& a, int64_t bx, int nthr, float2* sm) {
 // ---------------------------------------------------------------------------
 
 // X[k] = s_k xi_k of a 1-D field (xi real at the self-conjugate k = 0 and k = M).
-GRF_DEV float2 x1d(int k, int M, const float* __restrict__ stab, uint64_t key) {
-  return cscale(alg2_xi_1d(k, M, key), __ldg(stab + k));
+GRF_DEV float2 x1d(int k, int M, const float* __restrict__ stab, uint64_t key, const float2* trig) {
+  return cscale(alg2_xi_1d(k, M, key, trig), __ldg(stab + k));
 }
 
 template <int P>
@@ -439,7 +439,7 @@ GRF_DEV void fourstep1_body(const FourStepArgs& a, int bx, int64_t bz, int nthr,
   for (int q = 0; q < P; ++q) {
     const int k = k1 + a.A * (tau + TPT * q);
     const int mk = a.M - k;  // k = 0 pairs with X[M]
-    v[q] = c2r_pre(x1d(k, a.M, a.stab, key), x1d(mk, a.M, a.stab, key), __ldg(a.twN + k));
+    v[q] = c2r_pre(x1d(k, a.M, a.stab, key, a.trig), x1d(mk, a.M, a.stab, key, a.trig), __ldg(a.twN + k));
   }
   fft_core<P, +1>(v, sm, tau, c, C, a.B, a.logB, a.twB, a.tws, nthr);
   float2* Y = a.Y + field * (int64_t)a.M + ((k1 >> a.logT) * (int64_t)a.B << a.logT) + (k1 & (a.T - 1));

@@ -75,13 +75,24 @@ GRF_DEV double uniform_open_d(uint32_t x) {
 }
 
 // Box-Muller: rho = sqrt(-2 ln u_a), (z_re, z_im) = rho (cos 2 pi u_b, sin 2 pi u_b).
-// CUDA's accurate logf and sincospif are called (2 u_b is exact in FP32).
-GRF_DEV float2 box_muller(uint32_t wa, uint32_t wb) {
+// CUDA's accurate logf is called.  The angle: u_b = m' 2^-24 with m' = 2 (x >> 9) + 1
+// an odd 24-bit integer, so 2 pi u_b = a + delta exactly, with the coarse angle
+// a = 2 pi (m' >> 16) / 256 and delta = 2 pi (m' & 0xFFFF) 2^-24 in [0, 0.0246).
+// cos a, sin a come from `trig` (trig[h] = exp(2 pi i h / 256), built in FP64);
+// cos delta, sin delta from their Taylor series (truncation below 4e-13), and the
+// angle-addition formulas combine them.  Error: a few FP32 ulps.
+GRF_DEV float2 box_muller(uint32_t wa, uint32_t wb, const float2* __restrict__ trig) {
   const float ua = uniform_open(wa);
-  const float ub = uniform_open(wb);
-  const float rho = sqrtf(-2.0f * logf(ua));
-  float s, c;
-  sincospif(2.0f * ub, &s, &c);
+  const float rho2 = -2.0f * logf(ua);
+  const float rho = rho2 * rsqrtf(rho2);
+  const uint32_t m = (wb >> 9) * 2u + 1u;
+  const float2 t = __ldg(trig + (m >> 16));
+  const float dl = (float)(m & 0xFFFFu) * 3.7450703e-7f;  // 2 pi / 2^24
+  const float d2 = dl * dl;
+  const float cd = fmaf(d2, fmaf(d2, 1.0f / 24.0f, -0.5f), 1.0f);
+  const float sd = dl * fmaf(d2, fmaf(d2, 1.0f / 120.0f, -1.0f / 6.0f), 1.0f);
+  const float c = fmaf(t.x, cd, -t.y * sd);
+  const float s = fmaf(t.y, cd, t.x * sd);
   return make_float2(rho * c, rho * s);
 }
 GRF_DEV double2 box_muller_d(uint32_t wa, uint32_t wb) {
@@ -99,37 +110,38 @@ GRF_DEV double2 box_muller_d(uint32_t wa, uint32_t wb) {
 GRF_DEV uint64_t alg2_call_index(int k1, int kmid, int kd, int Nmid, int M) {
   return ((uint64_t)(k1 >> 1) * (uint64_t)Nmid + (uint64_t)kmid) * (uint64_t)(M + 1) + (uint64_t)kd;
 }
-GRF_DEV float2 alg2_normals_grid(int k1, int kmid, int kd, int Nmid, int M, uint64_t key) {
+GRF_DEV float2 alg2_normals_grid(int k1, int kmid, int kd, int Nmid, int M, uint64_t key, const float2* trig) {
   const u32x4 w = philox_call(alg2_call_index(k1, kmid, kd, Nmid, M), 0u, key);
-  return (k1 & 1) ? box_muller(w.z, w.w) : box_muller(w.x, w.y);
+  return (k1 & 1) ? box_muller(w.z, w.w, trig) : box_muller(w.x, w.y, trig);
 }
 GRF_DEV double2 alg2_normals_grid_d(int k1, int kmid, int kd, int Nmid, int M, uint64_t key) {
   const u32x4 w = philox_call(alg2_call_index(k1, kmid, kd, Nmid, M), 0u, key);
   return (k1 & 1) ? box_muller_d(w.z, w.w) : box_muller_d(w.x, w.y);
 }
-GRF_DEV float2 alg2_normals_1d(int kd, uint64_t key) {
+GRF_DEV float2 alg2_normals_1d(int kd, uint64_t key, const float2* trig) {
   const u32x4 w = philox_call((uint64_t)(kd >> 1), 0u, key);
-  return (kd & 1) ? box_muller(w.z, w.w) : box_muller(w.x, w.y);
+  return (kd & 1) ? box_muller(w.z, w.w, trig) : box_muller(w.x, w.y, trig);
 }
 
 // Hermitian noise xi_K of Algorithm 2 at a half-spectrum entry (k1, kmid, kd).
 // Off the planes kd in {0, M}: (z_re + i z_im)/sqrt 2.  On the planes: the member
 // of {K, -K} with the larger row-major index keeps its own normals, the other
 // takes the conjugate; a self-conjugate K takes the real normal z_re.
-GRF_DEV float2 alg2_xi_grid(int k1, int kmid, int kd, int N1, int Nmid, int M, uint64_t key) {
+GRF_DEV float2 alg2_xi_grid(int k1, int kmid, int kd, int N1, int Nmid, int M, uint64_t key,
+                            const float2* trig) {
   const float r2 = 0.70710678118654752440f;
   if (kd != 0 && kd != M) {
-    const float2 z = alg2_normals_grid(k1, kmid, kd, Nmid, M, key);
+    const float2 z = alg2_normals_grid(k1, kmid, kd, Nmid, M, key, trig);
     return make_float2(z.x * r2, z.y * r2);
   }
   const int nk1 = (N1 - k1) & (N1 - 1), nkm = (Nmid - kmid) & (Nmid - 1);
   const int row = k1 * Nmid + kmid, nrow = nk1 * Nmid + nkm;
-  if (row == nrow) return make_float2(alg2_normals_grid(k1, kmid, kd, Nmid, M, key).x, 0.0f);
+  if (row == nrow) return make_float2(alg2_normals_grid(k1, kmid, kd, Nmid, M, key, trig).x, 0.0f);
   if (row > nrow) {
-    const float2 z = alg2_normals_grid(k1, kmid, kd, Nmid, M, key);
+    const float2 z = alg2_normals_grid(k1, kmid, kd, Nmid, M, key, trig);
     return make_float2(z.x * r2, z.y * r2);
   }
-  const float2 z = alg2_normals_grid(nk1, nkm, kd, Nmid, M, key);
+  const float2 z = alg2_normals_grid(nk1, nkm, kd, Nmid, M, key, trig);
   return make_float2(z.x * r2, -z.y * r2);
 }
 GRF_DEV double2 alg2_xi_grid_d(int k1, int kmid, int kd, int N1, int Nmid, int M, uint64_t key) {
@@ -149,8 +161,8 @@ GRF_DEV double2 alg2_xi_grid_d(int k1, int kmid, int kd, int N1, int Nmid, int M
   return make_double2(z.x * r2, -z.y * r2);
 }
 // 1-D: the self-conjugate points are kd = 0 and kd = M; everything else is generic.
-GRF_DEV float2 alg2_xi_1d(int kd, int M, uint64_t key) {
-  const float2 z = alg2_normals_1d(kd, key);
+GRF_DEV float2 alg2_xi_1d(int kd, int M, uint64_t key, const float2* trig) {
+  const float2 z = alg2_normals_1d(kd, key, trig);
   if (kd == 0 || kd == M) return make_float2(z.x, 0.0f);
   const float r2 = 0.70710678118654752440f;
   return make_float2(z.x * r2, z.y * r2);
@@ -165,15 +177,15 @@ GRF_DEV double2 alg2_xi_1d_d(int kd, int M, uint64_t key) {
 
 // Real normal of Algorithm 1 at flat grid index j: call j >> 2, pair t = (j & 3) >> 1,
 // even j the cosine normal, odd j the sine normal.
-GRF_DEV float alg1_normal(uint64_t j, uint64_t key) {
+GRF_DEV float alg1_normal(uint64_t j, uint64_t key, const float2* trig) {
   const u32x4 w = philox_call(j >> 2, 1u, key);
-  const float2 z = ((j & 3) >> 1) ? box_muller(w.z, w.w) : box_muller(w.x, w.y);
+  const float2 z = ((j & 3) >> 1) ? box_muller(w.z, w.w, trig) : box_muller(w.x, w.y, trig);
   return (j & 1) ? z.y : z.x;
 }
 // Both reals of the pair (j even, j + 1) in one call.
-GRF_DEV float2 alg1_normal_pair(uint64_t j_even, uint64_t key) {
+GRF_DEV float2 alg1_normal_pair(uint64_t j_even, uint64_t key, const float2* trig) {
   const u32x4 w = philox_call(j_even >> 2, 1u, key);
-  return ((j_even & 3) >> 1) ? box_muller(w.z, w.w) : box_muller(w.x, w.y);
+  return ((j_even & 3) >> 1) ? box_muller(w.z, w.w, trig) : box_muller(w.x, w.y, trig);
 }
 GRF_DEV double alg1_normal_d(uint64_t j, uint64_t key) {
   const u32x4 w = philox_call(j >> 2, 1u, key);

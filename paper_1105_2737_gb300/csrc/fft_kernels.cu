@@ -20,16 +20,40 @@
 namespace grf {
 
 template <int P, int SRC, int MODE>
-__global__ void __launch_bounds__(512) col_kernel(ColArgs a) {
+__global__ void __launch_bounds__(256, 3) col_kernel(ColArgs a) {
   extern __shared__ float2 sm[];
   const int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   col_body<P, SRC, MODE>(a, blockIdx.x, blockIdx.y, blockIdx.z, blk, blockDim.x, sm);
 }
 
 template <int P, int SRC, int MODE>
-__global__ void __launch_bounds__(512) row_kernel(RowArgs a) {
+__global__ void __launch_bounds__(256, 3) row_kernel(RowArgs a) {
   extern __shared__ float2 sm[];
   row_body<P, SRC, MODE>(a, blockIdx.x, blockDim.x, sm);
+}
+
+// Grid-stride forms of the two 2-D/3-D passes: `gridDim.x` CTAs walk all
+// tiles, so a small grid leaves room on every SM for another kernel's CTAs
+// (the pipelined schedule runs one CTA per SM of each pass side by side).
+template <int P, int SRC, int MODE>
+__global__ void __launch_bounds__(512) col_kernel_gs(ColArgs a, int gx, int gy, int gz) {
+  extern __shared__ float2 sm[];
+  const int64_t n = (int64_t)gx * gy * gz;
+  for (int64_t t = blockIdx.x; t < n; t += gridDim.x) {
+    const int bx = (int)(t % gx);
+    const int64_t r = t / gx;
+    col_body<P, SRC, MODE>(a, bx, (int)(r % gy), r / gy, t, blockDim.x, sm);
+    __syncthreads();
+  }
+}
+
+template <int P, int SRC, int MODE>
+__global__ void __launch_bounds__(512) row_kernel_gs(RowArgs a, int64_t ntiles) {
+  extern __shared__ float2 sm[];
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    row_body<P, SRC, MODE>(a, t, blockDim.x, sm);
+    __syncthreads();
+  }
 }
 
 template <int P>
@@ -187,6 +211,49 @@ cudaError_t launch_fourstep(int stage, int P, const FourStepArgs& a, int64_t nfi
   switch (P) {
     case 16: return launch_fourstep_t<16>(stage, a, nfields, s);
     default: return cudaErrorInvalidValue;  // both factors are >= 16
+  }
+}
+
+template <int P>
+static cudaError_t launch_gs_t(int which, const ColArgs* ca, const RowArgs* ra, dim3 tiles, int ctas,
+                               cudaStream_t s) {
+  if (which == 0) {
+    const int threads = ca->C * ca->N / P;
+    const size_t smem = col_smem_bytes(ca->N, ca->C);
+    auto k = col_kernel_gs<P, COL_NOISE, COL_INV>;
+    cudaError_t e = prepare_kernel((const void*)k, threads, smem);
+    if (e != cudaSuccess) return e;
+    k<<<ctas, threads, smem, s>>>(*ca, tiles.x, tiles.y, tiles.z);
+  } else {
+    const int threads = ra->C * (ra->M / P);
+    const size_t smem = row_smem_bytes(ra->M, ra->C);
+    auto k = row_kernel_gs<P, ROW_LOAD_H, ROW_C2R>;
+    cudaError_t e = prepare_kernel((const void*)k, threads, smem);
+    if (e != cudaSuccess) return e;
+    k<<<ctas, threads, smem, s>>>(*ra, (int64_t)tiles.x);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_col_noise_gs(int P, const ColArgs& a, dim3 tiles, int ctas, cudaStream_t s) {
+  switch (P) {
+    case 2: return launch_gs_t<2>(0, &a, nullptr, tiles, ctas, s);
+    case 4: return launch_gs_t<4>(0, &a, nullptr, tiles, ctas, s);
+    case 8: return launch_gs_t<8>(0, &a, nullptr, tiles, ctas, s);
+    case 16: return launch_gs_t<16>(0, &a, nullptr, tiles, ctas, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_row_c2r_gs(int P, const RowArgs& a, int64_t ntiles, int ctas, cudaStream_t s) {
+  const dim3 t((unsigned)ntiles);
+  switch (P) {
+    case 1: return launch_gs_t<1>(1, nullptr, &a, t, ctas, s);
+    case 2: return launch_gs_t<2>(1, nullptr, &a, t, ctas, s);
+    case 4: return launch_gs_t<4>(1, nullptr, &a, t, ctas, s);
+    case 8: return launch_gs_t<8>(1, nullptr, &a, t, ctas, s);
+    case 16: return launch_gs_t<16>(1, nullptr, &a, t, ctas, s);
+    default: return cudaErrorInvalidValue;
   }
 }
 

@@ -34,6 +34,7 @@ struct HalfGeom {
   const float* stab;      // s_K on the folded half spectrum, [kd][fmid][f1]: (M+1) x (Nmid/2+1) x (N1/2+1)
   const float* dstab;     // d s_K / d(ell), d s_K / d(nu) (2 tables, same shape), adjoint only
   float inv_sigma;        // d s_K / d sigma = s_K / sigma, adjoint only
+  const float2* trig;     // exp(2 pi i h / 256), h < 256: coarse angles of Box-Muller
   float alg1_scale;       // 1 / sqrt(N_tot), Algorithm 1
 };
 
@@ -90,6 +91,7 @@ struct FourStepArgs {
   const float2* twN; // exp(2 pi i k / N), k < M
   const float2* tws;
   const float* stab; // s_k, k <= M
+  const float2* trig;  // exp(2 pi i h / 256)
   uint64_t seed;
   int64_t field0;
 };
@@ -99,6 +101,9 @@ cudaError_t launch_fourstep(int stage, int P, const FourStepArgs& a, int64_t nfi
 // transform (16 if the length is >= 16, else the length itself).
 cudaError_t launch_col(int src, int mode, int P, const ColArgs& a, dim3 grid, cudaStream_t s);
 cudaError_t launch_row(int src, int mode, int P, const RowArgs& a, dim3 grid, cudaStream_t s);
+// Grid-stride forms (ctas CTAs walk all tiles) of the noise + axis-1 pass and the c2r pass.
+cudaError_t launch_col_noise_gs(int P, const ColArgs& a, dim3 tiles, int ctas, cudaStream_t s);
+cudaError_t launch_row_c2r_gs(int P, const RowArgs& a, int64_t ntiles, int ctas, cudaStream_t s);
 size_t col_smem_bytes(int N, int C);
 // Dynamic shared memory and the L1/shared carveout of a kernel for a launch shape.
 cudaError_t prepare_kernel(const void* k, int threads, size_t smem);

@@ -14,6 +14,7 @@
 // contents; every call rebuilds what it reads before reading it.  Calls that
 // overlap on the GPU (several streams, or several host threads) race on the
 // array: keep calls of this entry point on one stream at a time.
+#include <algorithm>
 #include <mutex>
 
 #include "grf.h"
@@ -113,7 +114,7 @@ extern "C" grf_status grf_sample_2d_static(const int64_t* n, const double* L, co
   }
 
   const int N1 = (int)n[0], N2 = (int)n[1], M = N2 / 2;
-  const int maxlen = N1 > N2 ? N1 : N2;
+  const int maxlen = std::max(256, std::max(N1, N2));  // length 256: Box-Muller's coarse angles
   const size_t tw_bytes = align256((size_t)(2 * maxlen + kStageTableEntries) * sizeof(float2));
   const size_t fold = (size_t)(N1 / 2 + 1) * (M + 1);
   const size_t st_bytes = align256(fold * sizeof(float));
@@ -154,6 +155,7 @@ extern "C" grf_status grf_sample_2d_static(const int64_t* n, const double* L, co
   g.Q = (uint32_t)(M / 2 + 1);
   g.seed = seed;
   g.stab = stab;
+  g.trig = tw + 256;
   ColArgs a{};
   a.N = N1;
   a.logN = lg2(N1);
