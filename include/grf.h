@@ -130,6 +130,19 @@ grf_status grf_plan_create(grf_plan* out, int d, const int64_t* n, const double*
 grf_status grf_plan_set_spectrum(grf_plan p, const grf_spectrum* spec, void* stream);
 
 /*
+ * grf_plan_tune - choose the plan's schedules by timing them (no counterpart
+ * in the paper): for each pass the radix (4, 8 or 16 points per thread), the
+ * columns or rows per CTA, the row tile T of the 2-D workspace layout, and the
+ * pipelining depth, by coordinate descent with CUDA events on `stream`.  The
+ * winner is applied and stored in the tuning cache (GRF_TUNE_CACHE, default
+ * $HOME/.cache/grf_gb300_tune.txt) under the GPU name, grid, algorithm and
+ * max_batch; later grf_plan_create calls for the same key apply it.  Setting
+ * GRF_TUNE=1 makes grf_plan_create tune.  FP32 2-D and 3-D plans.  Allocates a
+ * temporary output of at most 64 MiB (or one field) while it runs.
+ */
+grf_status grf_plan_tune(grf_plan p, void* stream);
+
+/*
  * grf_sample - draw `batch` fields (§3 Algorithm 2, or Algorithm 1 if the plan
  * says so).  Field b uses Philox key seed + b.
  *   out : device pointer to batch * N_1 * ... * N_d floats (FP32 plan) or
@@ -286,7 +299,9 @@ int64_t grf_plan_timing_read(grf_plan p, int* kinds, float* ms, int64_t cap_out)
 
 /* grf_plan_query - sizes: 0 = points per field (batch plans: total points),
  * 1 = half-spectrum entries per field, 2 = workspace bytes, 3 = dimension d,
- * 4..6 = N_1..N_3.  Returns -1 for an unknown key or a NULL plan. */
+ * 4..6 = N_1..N_3, 7 = tile T, 8/9 = radix and columns per CTA of the axis-1
+ * pass, 10/11 = the same for the c2r pass, 12 = pipelining depth, 13/14 = the
+ * axis-2 pass (3-D).  Returns -1 for an unknown key or a NULL plan. */
 int64_t grf_plan_query(grf_plan p, int key);
 
 /* grf_plan_destroy - free the plan and everything it owns (NULL is allowed). */

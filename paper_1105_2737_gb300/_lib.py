@@ -54,6 +54,7 @@ def lib():
             "grf_plan_create": (C.c_int, [C.POINTER(P), C.c_int, C.POINTER(I64), C.POINTER(D),
                                           C.POINTER(grf_spectrum), C.c_int, C.c_int, I64]),
             "grf_plan_set_spectrum": (C.c_int, [P, C.POINTER(grf_spectrum), VP]),
+            "grf_plan_tune": (C.c_int, [P, VP]),
             "grf_sample": (C.c_int, [P, U64, I64, VP, VP]),
             "grf_sample_host": (C.c_int, [P, U64, I64, VP, VP]),
             "grf_backward": (C.c_int, [P, U64, I64, VP, VP, VP]),
@@ -110,6 +111,17 @@ def grf_plan_create(d, n, L, spec, alg=GRF_ALG_ONE_FFT, prec=GRF_FP32, max_batch
 
 def grf_plan_set_spectrum(plan, spec, stream=0):
     check(lib().grf_plan_set_spectrum(plan, C.byref(spec), C.c_void_p(stream)), "grf_plan_set_spectrum")
+
+
+def grf_plan_tune(plan, stream=0):
+    check(lib().grf_plan_tune(plan, C.c_void_p(stream)), "grf_plan_tune")
+
+
+SCHEDULE_KEYS = {"T": 7, "colA_P": 8, "colA_C": 9, "row_P": 10, "row_C": 11, "pipe": 12, "colB_P": 13, "colB_C": 14}
+
+
+def grf_plan_schedule(plan):
+    return {k: grf_plan_query(plan, v) for k, v in SCHEDULE_KEYS.items()}
 
 
 def grf_sample(plan, seed, batch, out_ptr, stream=0):

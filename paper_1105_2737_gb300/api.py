@@ -64,6 +64,16 @@ class GRF:
     def empty(self, batch: int) -> torch.Tensor:
         return torch.empty((batch,) + self.shape, dtype=self.dtype, device=self.device)
 
+    def tune(self) -> dict:
+        """Time the candidate schedules (radix, tiles, pipelining) and keep the best."""
+        with torch.cuda.device(self.device):
+            L.grf_plan_tune(self.handle, _stream_ptr(self.device))
+        return self.schedule
+
+    @property
+    def schedule(self) -> dict:
+        return L.grf_plan_schedule(self.handle)
+
     def sample(self, seed: int = 0, batch: int = 1, out: torch.Tensor | None = None) -> torch.Tensor:
         """batch fields; field b uses Philox key seed + b."""
         if out is None:

@@ -5,6 +5,7 @@
 #include "kernels.h"
 #include "plain64.h"
 #include "batch.h"
+#include "tune_cache.h"
 
 #include <algorithm>
 #include <cmath>
@@ -96,6 +97,29 @@ RowSched choose_row(int M, int64_t nrows, int max_threads = 256) {
   if (C > rp) C = (int)rp;
   s.C = C;
   return s;
+}
+
+int max_threads_for(int P) { return P >= 16 ? 256 : (P == 8 ? 512 : 1024); }
+
+// Schedules the tuner tries for transforms of length N over `ncols` columns
+// (or rows): radix P in {16, 8, 4} (P = N for the tiniest lengths), and every
+// power-of-two count of columns per CTA that fits the radix's thread limit.
+std::vector<ColSched> schedule_candidates(int N, int64_t ncols, bool rows) {
+  std::vector<ColSched> out;
+  for (int P : {16, 8, 4, 2, 1}) {
+    if (P > N || (P < 4 && P != N)) continue;
+    const int TPT = N / P;
+    const int maxC = max_threads_for(P) / TPT;
+    for (int C = 1; C <= maxC && C <= next_pow2(ncols); C *= 2) {
+      const size_t smem = rows ? row_smem_bytes(N, C) : col_smem_bytes(N, C);
+      if (smem > kSmemCap) break;
+      ColSched cs;
+      cs.P = P;
+      cs.C = C;
+      out.push_back(cs);
+    }
+  }
+  return out;
 }
 
 }  // namespace
@@ -365,6 +389,45 @@ dim3 row_grid(const RowArgs& r) { return dim3((unsigned)((r.nrows + r.C - 1) / r
     if (e_ != cudaSuccess) return cuda_fail(e_, where);      \
   } while (0)
 
+// Cache key of a plan's schedule: the GPU, the grid and the algorithm.
+std::string plan_key(const grf_plan_s* p) {
+  std::string k = "plan|" + tune_gpu_name() + "|" + std::to_string(p->d);
+  for (int i = 0; i < 3; ++i) k += "x" + std::to_string(p->n[i]);
+  k += "|alg" + std::to_string(p->alg) + "|b" + std::to_string(p->max_batch);
+  return k;
+}
+
+bool valid_sched(const ColSched& c, int N, int64_t ncols, bool rows) {
+  for (const ColSched& x : schedule_candidates(N, ncols, rows))
+    if (x.P == c.P && x.C == c.C) return true;
+  return false;
+}
+
+// Values: T, colA.P, colA.C, colB.P, colB.C, row.P, row.C, pipe.  Applied only
+// if every entry is a schedule this plan could have chosen itself.
+void apply_schedule(grf_plan_s* p, const std::vector<int>& v) {
+  if (v.size() != 8 || p->d < 2) return;
+  ColSched a, b, r;
+  a.P = v[1];
+  a.C = v[2];
+  b.P = v[3];
+  b.C = v[4];
+  r.P = v[5];
+  r.C = v[6];
+  const int T = v[0];
+  if (T < 1 || (T & (T - 1)) || p->N1 % T || (p->d == 3 && T != 1)) return;
+  if (!valid_sched(a, p->N1, (int64_t)p->Nmid * (p->M + 1), false)) return;
+  if (p->d == 3 && !valid_sched(b, p->Nmid, p->M + 1, false)) return;
+  if (!valid_sched(r, p->M, p->max_batch * (p->ntot / p->n[p->d - 1]), true)) return;
+  if (v[7] < 1 || v[7] > 8) return;
+  p->T = T;
+  p->colA = a;
+  if (p->d == 3) p->colB = b;
+  p->row.P = r.P;
+  p->row.C = r.C;
+  p->pipe = v[7];
+}
+
 // A launch bracketed by timing events when the plan records them.
 #define TLAUNCH(kind, call, where)                                                   \
   do {                                                                               \
@@ -593,6 +656,10 @@ grf_status grf_plan_create(grf_plan* out, int d, const int64_t* n, const double*
       }
       p->chunk = max_batch;
       PLAN_CUDA(dmalloc(&p->ws, (size_t)(p->chunk * p->hsize)), "workspace");
+      {  // a tuned schedule for this GPU and problem, if one was stored
+        std::vector<int> v;
+        if (tune_cache_lookup(plan_key(p), &v)) apply_schedule(p, v);
+      }
       if (const char* pe = std::getenv("GRF_PIPELINE")) p->pipe = std::max(1, std::min(8, std::atoi(pe)));
       if (const char* ge = std::getenv("GRF_GS_CTAS")) p->gs_ctas = std::max(0, std::min(8, std::atoi(ge)));
       cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
@@ -608,6 +675,8 @@ grf_status grf_plan_create(grf_plan* out, int d, const int64_t* n, const double*
   PLAN_CUDA(cudaStreamSynchronize(s), "plan table build");
 #undef PLAN_CUDA
   *out = p;
+  if (const char* te = std::getenv("GRF_TUNE"))
+    if (te[0] == '1' && prec == GRF_FP32 && d >= 2) grf_plan_tune(p, nullptr);
   return GRF_OK;
 }
 
@@ -681,6 +750,130 @@ grf_status grf_sample(grf_plan p, uint64_t seed, int64_t batch, void* out, void*
     if (st != GRF_OK) return st;
   }
   return GRF_OK;
+}
+
+grf_status grf_plan_tune(grf_plan p, void* stream) {
+  grf_status st = check_plan(p);
+  if (st != GRF_OK) return st;
+  if (p->kind != 0 || p->prec != GRF_FP32 || p->d < 2)
+    return fail(GRF_ERR_UNSUPPORTED, "the tuner covers FP32 2-D and 3-D plans");
+  cudaStream_t s = (cudaStream_t)stream;
+  // enough fields for a few waves of CTAs, within max_batch
+  int64_t bt = (int64_t)((64ll << 20) / p->ntot);
+  bt = std::max<int64_t>(1, std::min<int64_t>(bt, p->max_batch));
+  float* out = nullptr;
+  GRF_CUDA(cudaMalloc(&out, (size_t)bt * p->ntot * sizeof(float)), "tuning output");
+  const int64_t old_cap = p->tcap;
+  // mean time per launch kind over two timed calls (after one warm-up call)
+  auto measure = [&](double* ms_kind) -> grf_status {
+    for (int k = 0; k < 8; ++k) ms_kind[k] = 0.0;
+    grf_status r = grf_sample(p, 1, bt, out, stream);
+    if (r != GRF_OK) return r;
+    GRF_CUDA(cudaStreamSynchronize(s), "tuning sync");
+    r = grf_plan_timing(p, 64);
+    if (r != GRF_OK) return r;
+    for (int i = 0; i < 2 && r == GRF_OK; ++i) r = grf_sample(p, 2 + i, bt, out, stream);
+    if (r != GRF_OK) return r;
+    int kinds[64];
+    float ms[64];
+    const int64_t n = grf_plan_timing_read(p, kinds, ms, 64);
+    for (int64_t i = 0; i < n && i < 64; ++i)
+      if (kinds[i] >= 0 && kinds[i] < 8) ms_kind[kinds[i]] += ms[i] / 2.0;
+    return GRF_OK;
+  };
+  const int64_t ncolA = (int64_t)p->Nmid * (p->M + 1);
+  const int64_t nrows = p->max_batch * (p->ntot / p->n[p->d - 1]);
+  std::vector<int> tvals = {1};
+  if (p->d == 2)
+    for (int T = 2; T <= 16; T *= 2)
+      if (p->N1 % T == 0) tvals.push_back(T);
+  double best_total = 1e30;
+  std::vector<int> best;
+  double ms[8];
+  for (int T : tvals) {
+    p->T = T;
+    double total = 0.0;
+    ColSched ba = p->colA;
+    double bta = 1e30;
+    for (const ColSched& c : schedule_candidates(p->N1, ncolA, false)) {
+      p->colA = c;
+      if ((st = measure(ms)) != GRF_OK) break;
+      if (ms[GRF_KERNEL_NOISE_COLUMNS] < bta) {
+        bta = ms[GRF_KERNEL_NOISE_COLUMNS];
+        ba = c;
+      }
+    }
+    if (st != GRF_OK) break;
+    p->colA = ba;
+    total += bta;
+    if (p->d == 3) {
+      ColSched bb = p->colB;
+      double btb = 1e30;
+      for (const ColSched& c : schedule_candidates(p->Nmid, p->M + 1, false)) {
+        p->colB = c;
+        if ((st = measure(ms)) != GRF_OK) break;
+        if (ms[GRF_KERNEL_COLUMNS] < btb) {
+          btb = ms[GRF_KERNEL_COLUMNS];
+          bb = c;
+        }
+      }
+      if (st != GRF_OK) break;
+      p->colB = bb;
+      total += btb;
+    }
+    ColSched br;
+    br.P = p->row.P;
+    br.C = p->row.C;
+    double btr = 1e30;
+    for (const ColSched& c : schedule_candidates(p->M, nrows, true)) {
+      p->row.P = c.P;
+      p->row.C = c.C;
+      if ((st = measure(ms)) != GRF_OK) break;
+      if (ms[GRF_KERNEL_ROWS_C2R] < btr) {
+        btr = ms[GRF_KERNEL_ROWS_C2R];
+        br = c;
+      }
+    }
+    if (st != GRF_OK) break;
+    p->row.P = br.P;
+    p->row.C = br.C;
+    total += btr;
+    if (total < best_total) {
+      best_total = total;
+      best = {T, p->colA.P, p->colA.C, p->colB.P, p->colB.C, p->row.P, p->row.C, 1};
+    }
+  }
+  if (st == GRF_OK && !best.empty()) {
+    apply_schedule(p, best);
+    // pipelining depth, timed on whole calls
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float bestp = 1e30f;
+    int pipe_best = 1;
+    for (int pp : {1, 2, 4}) {
+      p->pipe = pp;
+      grf_sample(p, 1, bt, out, stream);
+      cudaEventRecord(e0, s);
+      for (int i = 0; i < 2; ++i) grf_sample(p, 2 + i, bt, out, stream);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float t = 1e30f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (t < bestp * 0.98f) {
+        bestp = t;
+        pipe_best = pp;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    best[7] = pipe_best;
+    apply_schedule(p, best);
+    tune_cache_store(plan_key(p), best);
+  }
+  grf_plan_timing(p, old_cap > 0 ? old_cap : 0);
+  cudaFree(out);
+  return st;
 }
 
 grf_status grf_sample_host(grf_plan p, uint64_t seed, int64_t batch, void* host_out, void* stream) {
@@ -963,6 +1156,14 @@ int64_t grf_plan_query(grf_plan p, int key) {
     case 4: return p->n[0];
     case 5: return p->n[1];
     case 6: return p->n[2];
+    case 7: return p->T;
+    case 8: return p->colA.P;
+    case 9: return p->colA.C;
+    case 10: return p->row.P;
+    case 11: return p->row.C;
+    case 12: return p->pipe;
+    case 13: return p->colB.P;
+    case 14: return p->colB.C;
     default: return -1;
   }
 }

@@ -22,19 +22,17 @@
 // name and the batch's shape signature.
 #include "batch.h"
 #include "bodies.cuh"
+#include "tune_cache.h"
 
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
-#include <fstream>
 #include <mutex>
 #include <sstream>
 #include <string>
 #include <vector>
-
-#include <sys/stat.h>
 
 namespace grf {
 
@@ -230,53 +228,6 @@ int tile_cols(int len, int64_t ncols, int target) {
   if (C > cp) C = (int)cp;
   if (C < cmin) C = cmin;
   return C;
-}
-
-std::string gpu_name() {
-  int dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceProp pr;
-  if (cudaGetDeviceProperties(&pr, dev) != cudaSuccess) return "unknown";
-  std::string s = pr.name;
-  for (char& c : s)
-    if (c == ' ' || c == '=' || c == '\n') c = '_';
-  return s;
-}
-
-std::string cache_path() {
-  const char* e = std::getenv("GRF_TUNE_CACHE");
-  if (e && *e) return e;
-  const char* h = std::getenv("HOME");
-  return std::string(h ? h : "/tmp") + "/.cache/grf_gb300_tune.txt";
-}
-
-std::mutex g_cache_mu;
-
-bool cache_lookup(const std::string& key, int* a, int* b) {
-  std::lock_guard<std::mutex> lock(g_cache_mu);
-  std::ifstream f(cache_path());
-  std::string line;
-  bool found = false;
-  while (std::getline(f, line)) {
-    std::istringstream is(line);
-    std::string k;
-    int x, y;
-    if (is >> k >> x >> y && k == key) {
-      *a = x;
-      *b = y;
-      found = true;  // the last entry wins
-    }
-  }
-  return found;
-}
-
-void cache_store(const std::string& key, int a, int b) {
-  std::lock_guard<std::mutex> lock(g_cache_mu);
-  const std::string path = cache_path();
-  const size_t slash = path.find_last_of('/');
-  if (slash != std::string::npos) mkdir(path.substr(0, slash).c_str(), 0755);  // best effort
-  std::ofstream f(path, std::ios::app);
-  if (f) f << key << " " << a << " " << b << "\n";
 }
 
 cudaError_t build_jobs(BatchPlan* b) {
@@ -520,7 +471,7 @@ cudaError_t tune(BatchPlan* b, uint64_t seed, cudaStream_t s, int* status) {
   cudaError_t e = build_jobs(b);
   if (e != cudaSuccess) return e;
   b->tuned = true;
-  cache_store(b->signature, bt, bc);
+  tune_cache_store(b->signature, {bt, bc});
   return cudaSuccess;
 }
 
@@ -548,7 +499,7 @@ grf_status batch_plan_build(BatchPlan** out, int64_t count, const int* d, const 
   int64_t stab_total = 0, ws_total = 0;
   int twmax = 256;  // the length-256 table also serves Box-Muller's coarse angles
   std::ostringstream sig;
-  sig << gpu_name() << "|" << count;
+  sig << "batch|" << tune_gpu_name() << "|" << count;
   uint64_t hsh = 1469598103934665603ull;
   for (int64_t i = 0; i < count; ++i) {
     FieldInfo& f = b->fields[i];
@@ -624,10 +575,11 @@ grf_status batch_plan_build(BatchPlan** out, int64_t count, const int* d, const 
     e = build_stab(b->stabs + f.stab_off, nullptr, sp, 0.0, 0);
   }
   if (e == cudaSuccess) {
-    int tt = 0, cps = 0;
-    if (cache_lookup(b->signature, &tt, &cps) && (tt == 128 || tt == 256) && cps >= 1 && cps <= 4) {
-      b->tile_threads = tt;
-      b->ctas_per_sm = cps;
+    std::vector<int> v;
+    if (tune_cache_lookup(b->signature, &v) && v.size() == 2 && (v[0] == 128 || v[0] == 256) && v[1] >= 1 &&
+        v[1] <= 4) {
+      b->tile_threads = v[0];
+      b->ctas_per_sm = v[1];
       b->tuned = true;
     }
     e = build_jobs(b);

@@ -148,13 +148,20 @@ GRF_DEV void last_small_stage(float2 (&v)[P], int tau, int TPT, const float2* __
   });
 }
 
-// C sequences of length N (runtime power of two, N = TPT * P, N >= P) per CTA.
+// Offset of the radix-P stage tables inside `tws` (radix 16, then 8, then 4).
+template <int P>
+__host__ __device__ constexpr int stage_table_offset() {
+  return P == 16 ? 0 : (P == 8 ? 4080 : 4080 + 4088);
+}
+
+// C sequences of length N (runtime power of two, N = TPT * P, N >= P) per CTA,
+// radix P in {4, 8, 16} (P = N <= 2 is a single butterfly).
 //   v   : this thread's points (positions tau + TPT q)
 //   sm  : shared buffer of at least spad(N) * C float2 (unused if N == P)
 //   tw  : tw[k] = exp(+2 pi i k / N), k < N (FP64-built, FP32-rounded)
-//   tws : radix-16 stage tables: for the stage of span Ns (16, then 256) the
-//         entries (r - 1) Ns + m = exp(+2 pi i m r / (16 Ns)), r = 1..15, m < Ns,
-//         so that the lanes of a warp (consecutive m) read consecutive entries
+//   tws : stage tables: for radix P and span Ns (P, P^2, ...) the entries
+//         (r - 1) Ns + m = exp(+2 pi i m r / (P Ns)), r = 1..P-1, m < Ns, so
+//         that the lanes of a warp (consecutive m) read consecutive entries
 //   nthr: threads taking part (C * N / P), the barrier count of every exchange
 // Every exchange starts with a barrier, so the caller may have used `sm` just
 // before; after return other threads may still read `sm`.
@@ -163,55 +170,72 @@ GRF_DEV void fft_core(float2 (&v)[P], float2* sm, int tau, int c, int C, int N, 
                       const float2* __restrict__ tw, const float2* __restrict__ tws, int nthr) {
   if constexpr (P == 1) {
     return;
-  } else if constexpr (P < 16) {
-    // N == P: a single in-register stage.
-    dft_regs<P, DIR, 1, 0>(v);
+  } else if constexpr (P == 2) {
+    dft_regs<2, DIR, 1, 0>(v);  // N == 2
   } else {
-    const int TPT = N >> 4;
-    const int n16 = logN >> 2;
-    const int rl = logN & 3;
+    constexpr int LP = ilog2c(P);
+    if (N == P) {  // a single in-register stage
+      dft_regs<P, DIR, 1, 0>(v);
+      return;
+    }
+    const int TPT = N >> LP;
+    const int nP = logN / LP;
+    const int rl = logN - nP * LP;
     // read positions tau + TPT q: spad is linear in q when TPT is a multiple of 16
     const int rd0 = spad(tau) * C + c;
     const int rdq = (TPT + (TPT >> 4)) * C;
+    const float2* tab = tws + stage_table_offset<P>();
     int Ns = 1;
     int off = 0;
-    float2 w[15];  // twiddles of the next radix-16 stage, loaded one stage ahead
-    for (int s = 0; s < n16; ++s) {
+    float2 w[P - 1];  // twiddles of the next stage, loaded one stage ahead
+    for (int s = 0; s < nP; ++s) {
       const int m = tau & (Ns - 1);
       if (Ns > 1) {
 #pragma unroll
-        for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], make_float2(w[r - 1].x, DIR > 0 ? w[r - 1].y : -w[r - 1].y));
+        for (int r = 1; r < P; ++r) v[r] = cmul(v[r], make_float2(w[r - 1].x, DIR > 0 ? w[r - 1].y : -w[r - 1].y));
       }
-      if (s + 1 < n16) {  // span of the next stage: 16 Ns
-        const float2* t = tws + off + (tau & (16 * Ns - 1));
+      if (s + 1 < nP) {  // span of the next stage: P Ns
+        const float2* t = tab + off + (tau & (P * Ns - 1));
 #pragma unroll
-        for (int r = 1; r < 16; ++r) w[r - 1] = __ldg(t + (r - 1) * (16 * Ns));
-        off += 15 * 16 * Ns;
+        for (int r = 1; r < P; ++r) w[r - 1] = __ldg(t + (r - 1) * (P * Ns));
+        off += (P - 1) * P * Ns;
       }
-      dft_regs<16, DIR, 1, 0>(v);
-      const bool last = (s == n16 - 1) && rl == 0;
+      dft_regs<P, DIR, 1, 0>(v);
+      const bool last = (s == nP - 1) && rl == 0;
       if (!last) {
-        // write positions (j / Ns) Ns 16 + j % Ns + r Ns, j = tau: spad is linear in r
-        const int base = (tau - m) * 16 + m;
-        const int wr0 = spad(base) * C + c;
-        const int wrr = (Ns + (Ns >> 4)) * C;
+        // write positions (j / Ns) Ns P + j % Ns + r Ns, j = tau; spad is linear
+        // in r when Ns = 1 or Ns is a multiple of 16
+        const int base = (tau - m) * P + m;
         cta_sync(nthr);
+        if (Ns == 1 || (Ns & 15) == 0) {
+          const int wr0 = spad(base) * C + c;
+          const int wrr = (Ns + (Ns >> 4)) * C;
 #pragma unroll
-        for (int r = 0; r < 16; ++r) sm[wr0 + r * wrr] = v[r];
-        cta_sync(nthr);
-        if (TPT >= 16) {
-#pragma unroll
-          for (int q = 0; q < 16; ++q) v[q] = sm[rd0 + q * rdq];
+          for (int r = 0; r < P; ++r) sm[wr0 + r * wrr] = v[r];
         } else {
 #pragma unroll
-          for (int q = 0; q < 16; ++q) v[q] = sm[spad(tau + TPT * q) * C + c];
+          for (int r = 0; r < P; ++r) sm[spad(base + r * Ns) * C + c] = v[r];
+        }
+        cta_sync(nthr);
+        if ((TPT & 15) == 0) {
+#pragma unroll
+          for (int q = 0; q < P; ++q) v[q] = sm[rd0 + q * rdq];
+        } else {
+#pragma unroll
+          for (int q = 0; q < P; ++q) v[q] = sm[spad(tau + TPT * q) * C + c];
         }
       }
-      Ns *= 16;
+      Ns *= P;
     }
-    if (rl == 1) last_small_stage<16, 2, DIR>(v, tau, TPT, tw);
-    else if (rl == 2) last_small_stage<16, 4, DIR>(v, tau, TPT, tw);
-    else if (rl == 3) last_small_stage<16, 8, DIR>(v, tau, TPT, tw);
+    if constexpr (P >= 4) {
+      if (rl == 1) last_small_stage<P, 2, DIR>(v, tau, TPT, tw);
+    }
+    if constexpr (P >= 8) {
+      if (rl == 2) last_small_stage<P, 4, DIR>(v, tau, TPT, tw);
+    }
+    if constexpr (P >= 16) {
+      if (rl == 3) last_small_stage<P, 8, DIR>(v, tau, TPT, tw);
+    }
   }
 }
 

@@ -19,15 +19,22 @@
 
 namespace grf {
 
+// Threads per CTA of each radix: 256 for radix 16 (3 CTAs per SM), 512 for
+// radix 8 (N = 4096 needs 512 threads of 8 points), 1024 for radix 4 and below.
+template <int P>
+constexpr int kMaxThreads = P >= 16 ? 256 : (P == 8 ? 512 : 1024);
+template <int P>
+constexpr int kMinBlocks = P >= 16 ? 3 : (P == 8 ? 2 : 1);
+
 template <int P, int SRC, int MODE>
-__global__ void __launch_bounds__(256, 3) col_kernel(ColArgs a) {
+__global__ void __launch_bounds__(kMaxThreads<P>, kMinBlocks<P>) col_kernel(ColArgs a) {
   extern __shared__ float2 sm[];
   const int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   col_body<P, SRC, MODE>(a, blockIdx.x, blockIdx.y, blockIdx.z, blk, blockDim.x, sm);
 }
 
 template <int P, int SRC, int MODE>
-__global__ void __launch_bounds__(256, 3) row_kernel(RowArgs a) {
+__global__ void __launch_bounds__(kMaxThreads<P>, kMinBlocks<P>) row_kernel(RowArgs a) {
   extern __shared__ float2 sm[];
   row_body<P, SRC, MODE>(a, blockIdx.x, blockDim.x, sm);
 }
@@ -75,7 +82,7 @@ __global__ void __launch_bounds__(512) fourstep_stage2(FourStepArgs a) {
 int points_per_thread(int n) { return n >= 16 ? 16 : n; }
 
 size_t col_smem_bytes(int N, int C) {
-  size_t e = (size_t)(N >= 16 ? spad_h(N) : 0) * C * sizeof(float2);
+  size_t e = (size_t)spad_h(N) * C * sizeof(float2);
   const size_t red = 3 * sizeof(double) * 32;  // block_sum3 scratch
   return e > red ? e : red;
 }

@@ -121,8 +121,9 @@ struct SpecParams {
   int d;
 };
 // tw[L + k] = exp(2 pi i k / L) for powers of two L <= maxlen, then (at
-// offset 2 maxlen) the radix-16 stage tables of spans 16 and 256 (15 Ns entries each).
-constexpr int kStageTableEntries = 15 * 16 + 15 * 256;
+// offset 2 maxlen) the stage tables: radix 16 (spans 16, 256), radix 8 (8, 64,
+// 512), radix 4 (4, 16, 64, 256, 1024), (P - 1) Ns entries per span.
+constexpr int kStageTableEntries = 15 * (16 + 256) + 7 * (8 + 64 + 512) + 3 * (4 + 16 + 64 + 256 + 1024);
 cudaError_t build_twiddles(float2* tw, int maxlen, cudaStream_t s);
 cudaError_t build_twiddles_d(double2* tw, int maxlen, cudaStream_t s);
 cudaError_t build_stab(float* stab, float* dstab, const SpecParams& sp, double dig_a_minus_nu,

@@ -38,16 +38,21 @@ __global__ void twiddle_kernel_d(double2* tw, int total) {
   tw[i] = make_double2(c, s);
 }
 
-// Stage tables: span Ns = 16 (240 entries) then Ns = 256 (3840 entries);
-// entry (r - 1) Ns + m = exp(2 pi i m r / (16 Ns)), r = 1..15, m < Ns.
+// Stage tables, per radix R in (16, 8, 4) and span Ns in (R, R^2, ...):
+// entry (r - 1) Ns + m = exp(2 pi i m r / (R Ns)), r = 1..R-1, m < Ns.
 __global__ void stage_table_kernel(float2* tws) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= kStageTableEntries) return;
-  const int Ns = i < 240 ? 16 : 256;
-  const int loc = i < 240 ? i : i - 240;
+  const int R = i < 4080 ? 16 : (i < 8168 ? 8 : 4);
+  int loc = i < 4080 ? i : (i < 8168 ? i - 4080 : i - 8168);
+  int Ns = R;
+  while (loc >= (R - 1) * Ns) {
+    loc -= (R - 1) * Ns;
+    Ns *= R;
+  }
   const int r = loc / Ns + 1, m = loc % Ns;
   double sn, cs;
-  sincospi(2.0 * (double)(m * r) / (double)(16 * Ns), &sn, &cs);
+  sincospi(2.0 * (double)((int64_t)m * r) / (double)(R * Ns), &sn, &cs);
   tws[i] = make_float2((float)cs, (float)sn);
 }
 

@@ -1,0 +1,89 @@
+"""Schedules: every radix (4, 8, 16 points per thread) and tile choice gives
+the oracle's fields, schedules stored in the tuning cache are applied by
+grf_plan_create, and grf_plan_tune picks a valid schedule."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import grf_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1105_2737_gb300 import build
+    build()
+
+
+def _key2(shape, alg, max_batch):
+    n = list(shape) + [1] * (3 - len(shape))
+    gpu = torch.cuda.get_device_name().replace(" ", "_")
+    return "plan|%s|%d" % (gpu, len(shape)) + "".join("x%d" % v for v in n) + "|alg%d|b%d" % (alg, max_batch)
+
+
+# (T, colA.P, colA.C, colB.P, colB.C, row.P, row.C, pipe)
+SCHEDS_2D = [(1, 16, 1, 16, 1, 16, 1, 1), (8, 8, 2, 16, 1, 8, 4, 1), (4, 4, 4, 16, 1, 4, 8, 2),
+             (16, 16, 4, 16, 1, 16, 2, 4), (2, 8, 1, 16, 1, 4, 1, 1)]
+
+
+@pytest.mark.parametrize("sched", SCHEDS_2D)
+def test_forced_schedules_2d(sched, tmp_path):
+    from paper_1105_2737_gb300 import api
+    shape, Lb, batch = (256, 512), (1.0, 1.0), 3
+    path = tmp_path / "tune.txt"
+    path.write_text(_key2(shape, 2, batch) + " " + " ".join(str(v) for v in sched) + "\n")
+    os.environ["GRF_TUNE_CACHE"] = str(path)
+    try:
+        g = api.GRF(shape, Lb, ell=0.05, nu=1.5, max_batch=batch)
+    finally:
+        del os.environ["GRF_TUNE_CACHE"]
+    sch = g.schedule
+    assert (sch["T"], sch["colA_P"], sch["colA_C"], sch["row_P"], sch["row_C"], sch["pipe"]) == \
+        (sched[0], sched[1], sched[2], sched[5], sched[6], sched[7])
+    f = g.sample(seed=4, batch=batch).cpu().numpy()
+    ref = O.sample(shape, Lb, O.Spectrum(O.MATERN, 1.0, 0.05, 1.5), 4, batch)
+    rel = np.linalg.norm(f - ref) / np.linalg.norm(ref)
+    assert rel <= 2e-6 and np.abs(f - ref).max() <= 1e-5, rel
+
+
+@pytest.mark.parametrize("sched", [(1, 8, 4, 4, 8, 8, 4, 1), (1, 4, 2, 8, 2, 16, 4, 2)])
+def test_forced_schedules_3d(sched, tmp_path):
+    from paper_1105_2737_gb300 import api
+    shape, Lb, batch = (32, 64, 64), (1.0, 1.0, 1.0), 2
+    path = tmp_path / "tune.txt"
+    path.write_text(_key2(shape, 2, batch) + " " + " ".join(str(v) for v in sched) + "\n")
+    os.environ["GRF_TUNE_CACHE"] = str(path)
+    try:
+        g = api.GRF(shape, Lb, family="gaussian", ell=0.05, max_batch=batch)
+    finally:
+        del os.environ["GRF_TUNE_CACHE"]
+    sch = g.schedule
+    assert (sch["colA_P"], sch["colB_P"], sch["row_P"]) == (sched[1], sched[3], sched[5])
+    f = g.sample(seed=6, batch=batch).cpu().numpy()
+    ref = O.sample(shape, Lb, O.Spectrum(O.GAUSSIAN, 1.0, 0.05, 0.0), 6, batch)
+    rel = np.linalg.norm(f - ref) / np.linalg.norm(ref)
+    assert rel <= 2e-6, rel
+
+
+def test_tune_picks_a_valid_schedule(tmp_path):
+    from paper_1105_2737_gb300 import api
+    os.environ["GRF_TUNE_CACHE"] = str(tmp_path / "tune.txt")
+    try:
+        g = api.GRF((512, 512), (1.0, 1.0), ell=0.05, nu=2.5, max_batch=16)
+        sch = g.tune()
+        assert sch["colA_P"] in (4, 8, 16) and sch["row_P"] in (4, 8, 16) and sch["T"] in (1, 2, 4, 8, 16)
+        text = (tmp_path / "tune.txt").read_text()
+        assert "plan|" in text
+        # a new plan with the same key picks the stored schedule up
+        g2 = api.GRF((512, 512), (1.0, 1.0), ell=0.05, nu=2.5, max_batch=16)
+        assert g2.schedule == sch
+    finally:
+        del os.environ["GRF_TUNE_CACHE"]
+    f = g2.sample(seed=1, batch=2).cpu().numpy()
+    ref = O.sample((512, 512), (1.0, 1.0), O.Spectrum(O.MATERN, 1.0, 0.05, 2.5), 1, 2)
+    assert np.linalg.norm(f - ref) / np.linalg.norm(ref) <= 2e-6
