@@ -301,7 +301,9 @@ int64_t grf_plan_timing_read(grf_plan p, int* kinds, float* ms, int64_t cap_out)
  * 1 = half-spectrum entries per field, 2 = workspace bytes, 3 = dimension d,
  * 4..6 = N_1..N_3, 7 = tile T, 8/9 = radix and columns per CTA of the axis-1
  * pass, 10/11 = the same for the c2r pass, 12 = pipelining depth, 13/14 = the
- * axis-2 pass (3-D).  Returns -1 for an unknown key or a NULL plan. */
+ * axis-2 pass (3-D), 15 = 1 if the c2r pass is the persistent kernel fed by
+ * bulk asynchronous copies (else the plain row kernel).  Returns -1 for an
+ * unknown key or a NULL plan. */
 int64_t grf_plan_query(grf_plan p, int key);
 
 /* grf_plan_destroy - free the plan and everything it owns (NULL is allowed). */

@@ -117,7 +117,8 @@ def grf_plan_tune(plan, stream=0):
     check(lib().grf_plan_tune(plan, C.c_void_p(stream)), "grf_plan_tune")
 
 
-SCHEDULE_KEYS = {"T": 7, "colA_P": 8, "colA_C": 9, "row_P": 10, "row_C": 11, "pipe": 12, "colB_P": 13, "colB_C": 14}
+SCHEDULE_KEYS = {"T": 7, "colA_P": 8, "colA_C": 9, "row_P": 10, "row_C": 11, "pipe": 12, "colB_P": 13, "colB_C": 14,
+                 "row_tma": 15}
 
 
 def grf_plan_schedule(plan):

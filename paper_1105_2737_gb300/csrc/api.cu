@@ -156,6 +156,7 @@ struct grf_plan_s {
   // 2-D / 3-D pipelining: the batch in `pipe` chunks, first passes on the
   // caller's stream, the others on tail_stream
   int pipe = 1;
+  int row_tma = 0;  // c2r pass: 0 = row kernel, 1 = persistent kernel fed by bulk async copies
   int gs_ctas = 1;  // grid-stride CTAs per SM of each pass when pipelined (0: full grids)
   int num_sms = 0;
   cudaStream_t tail_stream = nullptr;
@@ -378,8 +379,17 @@ RowArgs row_args(const grf_plan_s* p, const HalfGeom& g, int64_t nfields, int T)
   return r;
 }
 
+// Pair mode for the last column pass of a plane of M + 1 columns: it writes Z
+// of the c2r split (see col_body), which the c2r pass reads.
+ColArgs zpair(const grf_plan_s* p, ColArgs a) {
+  a.zpair = 1;
+  a.twz = twp(p, 2 * p->M);
+  return a;
+}
+
 dim3 col_grid(const ColArgs& a, int64_t planes, int64_t nfields) {
-  return dim3((unsigned)((a.ncols + a.C - 1) / a.C), (unsigned)planes, (unsigned)nfields);
+  const int64_t slots = a.zpair ? a.g.M / 2 + 1 : a.ncols;
+  return dim3((unsigned)((slots + a.C - 1) / a.C), (unsigned)planes, (unsigned)nfields);
 }
 dim3 row_grid(const RowArgs& r) { return dim3((unsigned)((r.nrows + r.C - 1) / r.C)); }
 
@@ -403,10 +413,13 @@ bool valid_sched(const ColSched& c, int N, int64_t ncols, bool rows) {
   return false;
 }
 
-// Values: T, colA.P, colA.C, colB.P, colB.C, row.P, row.C, pipe.  Applied only
-// if every entry is a schedule this plan could have chosen itself.
+// Values: T, colA.P, colA.C, colB.P, colB.C, row.P, row.C, pipe, row_tma
+// (absent: 0).  Applied only if every entry is a schedule this plan could have
+// chosen itself.
 void apply_schedule(grf_plan_s* p, const std::vector<int>& v) {
-  if (v.size() != 8 || p->d < 2) return;
+  if ((v.size() != 8 && v.size() != 9) || p->d < 2) return;
+  const int tma = v.size() == 9 ? v[8] : 0;
+  if (tma < 0 || tma > 1) return;
   ColSched a, b, r;
   a.P = v[1];
   a.C = v[2];
@@ -426,6 +439,7 @@ void apply_schedule(grf_plan_s* p, const std::vector<int>& v) {
   p->row.P = r.P;
   p->row.C = r.C;
   p->pipe = v[7];
+  p->row_tma = tma;
 }
 
 // A launch bracketed by timing events when the plan records them.
@@ -490,6 +504,7 @@ grf_status sample_chunk_fp32(grf_plan p, uint64_t seed, int64_t f0, int64_t nb, 
   const bool gs = st && st != s && p->gs_ctas > 0;
   if (p->alg == 2) {
     ColArgs a = col_axis1(p, g, nullptr, ws, T);
+    if (p->d == 2) a = zpair(p, a);
     if (gs)
       TLAUNCH(GRF_KERNEL_NOISE_COLUMNS, launch_col_noise_gs(p->colA.P, a, col_grid(a, 1, nb), p->gs_ctas * p->num_sms, s),
               "noise + axis-1 pass");
@@ -505,6 +520,7 @@ grf_status sample_chunk_fp32(grf_plan p, uint64_t seed, int64_t f0, int64_t nb, 
       TLAUNCH(GRF_KERNEL_COLUMNS, launch_col(COL_LOAD, COL_FWD, p->colB.P, b, col_grid(b, p->N1, nb), s), "alg1 axis-2 forward");
     }
     ColArgs a = col_axis1(p, g, ws, ws, T);
+    if (p->d == 2) a = zpair(p, a);
     TLAUNCH(GRF_KERNEL_COLUMNS, launch_col(COL_LOAD, COL_FWD_SCALE_INV, p->colA.P, a, col_grid(a, 1, nb), s), "alg1 axis-1 scale");
   }
   if (st && st != s) {
@@ -513,17 +529,20 @@ grf_status sample_chunk_fp32(grf_plan p, uint64_t seed, int64_t f0, int64_t nb, 
     s = st;
   }
   if (p->d == 3) {
-    ColArgs b = col_axis2(p, g, ws, ws);
+    ColArgs b = zpair(p, col_axis2(p, g, ws, ws));
     TLAUNCH(GRF_KERNEL_COLUMNS, launch_col(COL_LOAD, COL_INV, p->colB.P, b, col_grid(b, p->N1, nb), s), "axis-2 inverse");
   }
   RowArgs r = row_args(p, g, nb, T);
   r.inH = ws;
   r.outR = out;
-  if (gs)
+  if (p->row_tma && c2r_tma_ok(r))
+    TLAUNCH(GRF_KERNEL_ROWS_C2R, launch_row_c2r_tma(p->row.P, r, gs ? p->gs_ctas : 0, p->num_sms, p->status, s),
+            "c2r pass (bulk copies)");
+  else if (gs)
     TLAUNCH(GRF_KERNEL_ROWS_C2R, launch_row_c2r_gs(p->row.P, r, row_grid(r).x, p->gs_ctas * p->num_sms, s),
             "c2r pass");
   else
-    TLAUNCH(GRF_KERNEL_ROWS_C2R, launch_row(ROW_LOAD_H, ROW_C2R, p->row.P, r, row_grid(r), s), "c2r pass");
+    TLAUNCH(GRF_KERNEL_ROWS_C2R, launch_row(ROW_LOAD_Z, ROW_C2R, p->row.P, r, row_grid(r), s), "c2r pass");
   return GRF_OK;
 }
 
@@ -824,23 +843,35 @@ grf_status grf_plan_tune(grf_plan p, void* stream) {
     ColSched br;
     br.P = p->row.P;
     br.C = p->row.C;
+    int btma = 0;
     double btr = 1e30;
     for (const ColSched& c : schedule_candidates(p->M, nrows, true)) {
       p->row.P = c.P;
       p->row.C = c.C;
-      if ((st = measure(ms)) != GRF_OK) break;
-      if (ms[GRF_KERNEL_ROWS_C2R] < btr) {
-        btr = ms[GRF_KERNEL_ROWS_C2R];
-        br = c;
+      for (int tma = 0; tma <= 1 && st == GRF_OK; ++tma) {
+        if (tma) {  // only where the tuning batch takes the bulk-copy kernel
+          RowArgs r = row_args(p, half_geom(p, 0, 0), bt, p->d == 2 ? T : 1);
+          r.inH = p->ws;
+          if (!c2r_tma_ok(r)) continue;
+        }
+        p->row_tma = tma;
+        if ((st = measure(ms)) != GRF_OK) break;
+        if (ms[GRF_KERNEL_ROWS_C2R] < btr) {
+          btr = ms[GRF_KERNEL_ROWS_C2R];
+          br = c;
+          btma = tma;
+        }
       }
+      if (st != GRF_OK) break;
     }
     if (st != GRF_OK) break;
     p->row.P = br.P;
     p->row.C = br.C;
+    p->row_tma = btma;
     total += btr;
     if (total < best_total) {
       best_total = total;
-      best = {T, p->colA.P, p->colA.C, p->colB.P, p->colB.C, p->row.P, p->row.C, 1};
+      best = {T, p->colA.P, p->colA.C, p->colB.P, p->colB.C, p->row.P, p->row.C, 1, btma};
     }
   }
   if (st == GRF_OK && !best.empty()) {
@@ -1164,6 +1195,7 @@ int64_t grf_plan_query(grf_plan p, int key) {
     case 12: return p->pipe;
     case 13: return p->colB.P;
     case 14: return p->colB.C;
+    case 15: return p->row_tma;
     default: return -1;
   }
 }

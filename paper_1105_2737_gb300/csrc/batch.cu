@@ -98,11 +98,14 @@ GRF_DEV int wait_counter(const int* ctr, int need, const BatchParams& b) {
 __device__ __noinline__ void run_col_noise(const ColArgs& a, int bx, int by, int nthr, float2* sm) {
   col_body<16, COL_NOISE, COL_INV>(a, bx, by, 0, 0, nthr, sm);
 }
-__device__ __noinline__ void run_col_load(const ColArgs& a, int bx, int by, int nthr, float2* sm) {
-  col_body<16, COL_LOAD, COL_INV>(a, bx, by, 0, 0, nthr, sm);
+__device__ __noinline__ void run_col_noise_pair(const ColArgs& a, int bx, int by, int nthr, float2* sm) {
+  col_body_pair<16, COL_NOISE, COL_INV>(a, CtaCoordsVal{bx, by, 0}, nthr, sm);
+}
+__device__ __noinline__ void run_col_load_pair(const ColArgs& a, int bx, int by, int nthr, float2* sm) {
+  col_body_pair<16, COL_LOAD, COL_INV>(a, CtaCoordsVal{bx, by, 0}, nthr, sm);
 }
 __device__ __noinline__ void run_row_c2r(const RowArgs& a, int bx, int nthr, float2* sm) {
-  row_body<16, ROW_LOAD_H, ROW_C2R>(a, bx, nthr, sm);
+  row_body<16, ROW_LOAD_Z, ROW_C2R>(a, bx, nthr, sm);
 }
 __device__ __noinline__ void run_fs1(const FourStepArgs& a, int bx, int nthr, float2* sm) {
   fourstep1_body<16>(a, bx, 0, nthr, sm);
@@ -145,8 +148,11 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(BatchParams b) 
     const int nthr = s_job.nthr;
     if (t < nthr) {
       switch (s_job.kind) {
-        case JOB_COL_NOISE: run_col_noise(s_job.col, bx, by, nthr, sm); break;
-        case JOB_COL_LOAD: run_col_load(s_job.col, bx, by, nthr, sm); break;
+        case JOB_COL_NOISE:
+          if (s_job.col.zpair) run_col_noise_pair(s_job.col, bx, by, nthr, sm);
+          else run_col_noise(s_job.col, bx, by, nthr, sm);
+          break;
+        case JOB_COL_LOAD: run_col_load_pair(s_job.col, bx, by, nthr, sm); break;
         case JOB_ROW_C2R: run_row_c2r(s_job.row, bx, nthr, sm); break;
         case JOB_FS1: run_fs1(s_job.fs, bx, nthr, sm); break;
         default: run_fs2(s_job.fs, bx, nthr, sm); break;
@@ -309,13 +315,20 @@ cudaError_t build_jobs(BatchPlan* b) {
     a.tw = b->tw + g.N1;
     a.tws = tws;
     a.g = g;
+    int64_t slots = a.ncols;
+    if (d == 2) {  // the last column pass writes Z of the c2r split
+      a.zpair = 1;
+      a.twz = b->tw + Nd;
+      slots = M / 2 + 1;
+      a.C = tile_cols(a.N, slots, b->tile_threads);
+    }
     Job ja{};
     ja.kind = JOB_COL_NOISE;
     ja.pass = 0;
     ja.field = (int)i;
     ja.col = a;
     ja.nthr = a.C * a.N / 16;
-    ja.gx = (int)((a.ncols + a.C - 1) / a.C);
+    ja.gx = (int)((slots + a.C - 1) / a.C);
     int prev = add(ja, ja.gx);
     int pass = 1;
     if (d == 3) {
@@ -323,7 +336,9 @@ cudaError_t build_jobs(BatchPlan* b) {
       a2.N = g.Nmid;
       a2.logN = lg2(g.Nmid);
       a2.ncols = M + 1;
-      a2.C = tile_cols(a2.N, a2.ncols, b->tile_threads);
+      a2.zpair = 1;  // the last column pass writes Z of the c2r split
+      a2.twz = b->tw + Nd;
+      a2.C = tile_cols(a2.N, M / 2 + 1, b->tile_threads);
       a2.T = 1;
       a2.logT = 0;
       a2.ostride = (int64_t)g.Nmid * (M + 1);
@@ -338,7 +353,7 @@ cudaError_t build_jobs(BatchPlan* b) {
       jb.field = (int)i;
       jb.col = a2;
       jb.nthr = a2.C * a2.N / 16;
-      jb.gx = (int)((a2.ncols + a2.C - 1) / a2.C);
+      jb.gx = (int)((M / 2 + 1 + a2.C - 1) / a2.C);
       jb.need_prev = prev;
       prev = add(jb, jb.gx * g.N1);
       pass = 2;
@@ -381,7 +396,8 @@ cudaError_t build_jobs(BatchPlan* b) {
   size_t smem = 3 * 32 * sizeof(double);
   for (const Job& j : jobs) {
     size_t need = 0;
-    if (j.kind == JOB_COL_NOISE || j.kind == JOB_COL_LOAD) need = col_smem_bytes(j.col.N, j.col.C);
+    if (j.kind == JOB_COL_NOISE || j.kind == JOB_COL_LOAD)
+      need = j.col.zpair ? col_pair_smem_bytes(j.col.N, j.col.C) : col_smem_bytes(j.col.N, j.col.C);
     else if (j.kind == JOB_ROW_C2R) need = row_smem_bytes(j.row.M, j.row.C);
     else need = col_smem_bytes(j.kind == JOB_FS1 ? j.fs.B : j.fs.A, j.fs.C);
     smem = std::max(smem, need);

@@ -108,38 +108,33 @@ GRF_DEV void alg2_column_normals(float2 (&v)[P], int tau, int TPT, int C, int km
 // Column pass
 // ---------------------------------------------------------------------------
 
-template <int P, int SRC, int MODE>
-GRF_DEV void col_body(const ColArgs& a, int bx, int by, int64_t bz, int64_t blk, int nthr, float2* sm) {
-  const int C = a.C;
-  const int t = threadIdx.x;
-  const int c = t & (C - 1);
-  const int tau = t / C;
-  const int TPT = a.N / P;
-  const int col = bx * C + c;
-  const bool valid = col < a.ncols;
-  const int64_t field = bz;
-  const int64_t base = field * a.bstride + (int64_t)by * a.ostride;
-  // in-field offset of (pos, col): (pos >> logT) * (ncols << logT) + (col << logT) + (pos & (T - 1))
-  const int rowstride = a.ncols << a.logT;
-  const int colpart = col << a.logT;
-  const int tmask = a.T - 1;
+// Element (pos, col) of a plane in the tiled layout [pos / T][col][pos % T].
+GRF_DEV int64_t col_offset(const ColArgs& a, int pos, int col) {
+  return (int64_t)(pos >> a.logT) * (a.ncols << a.logT) + ((int64_t)col << a.logT) + (pos & (a.T - 1));
+}
 
-  ColGeom cg{0, 0};
+// Column `col` of the pass through its transforms: v[q] holds entry
+// pos = tau + TPT q.  `base` is the offset of the column's plane and field.
+template <int P, int SRC, int MODE>
+GRF_DEV void col_transform(const ColArgs& a, int col, bool valid, int64_t field, int64_t base, int tau, int c,
+                           int C, int nthr, float2* sm, float2 (&v)[P], ColGeom& cg) {
+  const int TPT = a.N / P;
+  cg = ColGeom{0, 0};
   if (SRC == COL_NOISE || MODE == COL_FWD_SCALE_INV || MODE == COL_FWD_ADJ) cg = col_geom(valid ? col : 0, a.g);
 
-  float2 v[P];
   if constexpr (SRC == COL_NOISE) {
     const HalfGeom& g = a.g;
     const uint64_t key = g.seed + (uint64_t)(g.field0 + field);
     // s_K of this column: the folded table row (kd, fmid) is contiguous along axis 1
     const float* srow = g.stab + (cg.kd * (g.Nmid / 2 + 1) + min(cg.kmid, g.Nmid - cg.kmid)) * (g.N1 / 2 + 1);
+    alg2_column_normals<P>(v, tau, TPT, C, cg.kmid, cg.kd, g, key);
+    // s_K read after the normals: the loads do not hold registers during the draw
     float s[P];
 #pragma unroll
     for (int q = 0; q < P; ++q) {
       const int k1 = tau + TPT * q;
       s[q] = __ldg(srow + min(k1, g.N1 - k1));
     }
-    alg2_column_normals<P>(v, tau, TPT, C, cg.kmid, cg.kd, g, key);
     const float r2 = 0.70710678118654752440f;
     if (cg.kd != 0 && cg.kd != g.M) {
 #pragma unroll
@@ -168,11 +163,8 @@ GRF_DEV void col_body(const ColArgs& a, int bx, int by, int64_t bz, int64_t blk,
     }
   } else {
 #pragma unroll
-    for (int q = 0; q < P; ++q) {
-      const int pos = tau + TPT * q;
-      v[q] = valid ? __ldcg(a.in + base + (int64_t)((pos >> a.logT) * rowstride + colpart + (pos & tmask)))
-                   : make_float2(0.f, 0.f);
-    }
+    for (int q = 0; q < P; ++q)
+      v[q] = valid ? __ldcg(a.in + base + col_offset(a, tau + TPT * q, col)) : make_float2(0.f, 0.f);
   }
 
   if constexpr (MODE == COL_INV) {
@@ -190,6 +182,114 @@ GRF_DEV void col_body(const ColArgs& a, int bx, int by, int64_t bz, int64_t blk,
     }
     fft_core<P, +1>(v, sm, tau, c, C, a.N, a.logN, a.tw, a.tws, nthr);
   }
+}
+
+// Pair mode (a.zpair), the last column pass before the c2r pass: one CTA
+// takes C column pairs of plane `by` of field `bz`.  Slot p <= M/2 takes the
+// columns kd = p and kd = M - p and writes, instead of X, the sequence the
+// M-point inverse FFT of the c2r split consumes:
+//   Z[p]     = (X[p] + conj X[M-p]) + i w (X[p] - conj X[M-p]),   w = e^{2 pi i p / N_d}
+//   Z[M - p] = conj(X[p] + conj X[M-p]) + i conj(w (X[p] - conj X[M-p]))
+// (the second is the first with p -> M - p, since e^{2 pi i (M-p)/N_d} = -conj w).
+// Pair 0 (columns 0 and M) gives Z[0] only and pair M/2 is one column.  Z[k]
+// lands where X[k] was (k < M; the slot of k = M is left unused), so the pass
+// may run in place.  X of column p waits in shared memory, after the
+// transform's exchange buffer, in a slot private to each thread
+// (col_pair_smem_bytes), while column M - p is transformed.
+//
+// The indices of the pair are formed afresh after each transform (from the
+// special registers in the per-pass kernels), so that nothing but the
+// transform's own state is live while it runs.
+struct CtaCoordsHW {  // per-pass kernels: blockIdx and threadIdx, re-read on each use
+  GRF_DEV int bx() const { unsigned r; asm volatile("mov.u32 %0, %%ctaid.x;" : "=r"(r)); return (int)r; }
+  GRF_DEV int by() const { unsigned r; asm volatile("mov.u32 %0, %%ctaid.y;" : "=r"(r)); return (int)r; }
+  GRF_DEV int64_t bz() const { unsigned r; asm volatile("mov.u32 %0, %%ctaid.z;" : "=r"(r)); return (int64_t)r; }
+  GRF_DEV int tid() const { unsigned r; asm volatile("mov.u32 %0, %%tid.x;" : "=r"(r)); return (int)r; }
+};
+struct CtaCoordsVal {  // persistent kernels: the tile's coordinates as values
+  int x, y;
+  int64_t z;
+  GRF_DEV int bx() const { return x; }
+  GRF_DEV int by() const { return y; }
+  GRF_DEV int64_t bz() const { return z; }
+  GRF_DEV int tid() const { return (int)threadIdx.x; }
+};
+
+struct PairIdx {
+  int c, tau, p, ca, cb;
+  bool valid;
+  int64_t field, base;
+};
+template <class Coords>
+GRF_DEV PairIdx pair_idx(const ColArgs& a, const Coords& co) {
+  PairIdx r;
+  const int t = co.tid();
+  r.c = t & (a.C - 1);
+  r.tau = t / a.C;
+  r.p = co.bx() * a.C + r.c;
+  r.valid = r.p <= a.g.M / 2;
+  r.ca = r.valid ? r.p : 0;
+  r.cb = r.valid ? a.g.M - r.p : 0;
+  r.field = co.bz();
+  r.base = r.field * a.bstride + (int64_t)co.by() * a.ostride;
+  return r;
+}
+
+template <int P, int SRC, int MODE, class Coords>
+GRF_DEV void col_body_pair(const ColArgs& a, const Coords& co, int nthr, float2* sm) {
+  static_assert(MODE == COL_INV || MODE == COL_FWD_SCALE_INV, "pair mode ends an inverse pass");
+  const int TPT = a.N / P;
+  float2 v[P];
+  ColGeom cg;
+  {
+    const PairIdx x = pair_idx(a, co);
+    col_transform<P, SRC, MODE>(a, x.ca, x.valid, x.field, x.base, x.tau, x.c, a.C, nthr, sm, v, cg);
+  }
+  float2* stash = sm + (size_t)spad(a.N) * a.C + co.tid();
+#pragma unroll
+  for (int q = 0; q < P; ++q) stash[q * nthr] = v[q];
+  {
+    // pair M/2 is one column: its second transform only keeps the CTA's
+    // barriers in step (an in-place pass has already replaced its input)
+    const PairIdx x = pair_idx(a, co);
+    col_transform<P, SRC, MODE>(a, x.cb, x.valid && x.ca != x.cb, x.field, x.base, x.tau, x.c, a.C, nthr, sm, v,
+                                cg);
+  }
+  const PairIdx x = pair_idx(a, co);
+  if (!x.valid) return;
+  float2* out = a.out + x.base;
+  const float2 w = __ldg(a.twz + x.p);
+  stash = sm + (size_t)spad(a.N) * a.C + co.tid();
+#pragma unroll
+  for (int q = 0; q < P; ++q) {
+    const int64_t oa = col_offset(a, x.tau + TPT * q, x.ca);
+    const float2 xa = stash[q * nthr];
+    const float2 xb = x.ca == x.cb ? xa : v[q];
+    const float2 A = make_float2(xa.x + xb.x, xa.y - xb.y);
+    const float2 B = make_float2(xa.x - xb.x, xa.y + xb.y);
+    const float2 wB = cmul(w, B);
+    out[oa] = make_float2(A.x - wB.y, A.y + wB.x);
+    if (x.p != 0 && x.ca != x.cb) out[col_offset(a, x.tau + TPT * q, x.cb)] = make_float2(A.x + wB.y, wB.x - A.y);
+  }
+}
+
+// One CTA: C columns of plane `by` of field `bz`, X stored (or, for the
+// adjoint, reduced).
+template <int P, int SRC, int MODE>
+GRF_DEV void col_body(const ColArgs& a, int bx, int by, int64_t bz, int64_t blk, int nthr, float2* sm) {
+  const int C = a.C;
+  const int t = threadIdx.x;
+  const int c = t & (C - 1);
+  const int tau = t / C;
+  const int TPT = a.N / P;
+  const int64_t field = bz;
+  const int64_t base = field * a.bstride + (int64_t)by * a.ostride;
+  float2 v[P];
+  ColGeom cg;
+
+  const int col = bx * C + c;
+  const bool valid = col < a.ncols;
+  col_transform<P, SRC, MODE>(a, col, valid, field, base, tau, c, C, nthr, sm, v, cg);
 
   if constexpr (MODE == COL_FWD_ADJ) {
     // v[q] = G^ at K = (k1, kmid, kd).  Sum w_K d_theta s_K Re(xi_K conj G^_K).
@@ -215,10 +315,7 @@ GRF_DEV void col_body(const ColArgs& a, int bx, int by, int64_t bz, int64_t blk,
 
   if (valid) {
 #pragma unroll
-    for (int q = 0; q < P; ++q) {
-      const int pos = tau + TPT * q;
-      a.out[base + (int64_t)((pos >> a.logT) * rowstride + colpart + (pos & tmask))] = v[q];
-    }
+    for (int q = 0; q < P; ++q) a.out[base + col_offset(a, tau + TPT * q, col)] = v[q];
   }
 }
 
@@ -265,25 +362,32 @@ GRF_DEV void row_body(const RowArgs& a, int64_t bx, int nthr, float2* sm) {
   const int64_t rowf = valid ? g - field * a.rows_per_field : 0;
   float2 v[P];
 
-  if constexpr (MODE == ROW_C2R) {
-    // Stage X[0..M] of every row of the CTA in shared memory (all loads first).
-    const int64_t hb = hrow_base(g, M, a.logT);
+  if constexpr (MODE == ROW_C2R && SRC == ROW_LOAD_Z) {
+    // Z[0..M-1] of the c2r split, formed by the last column pass: straight
+    // into the M-point inverse FFT.
+    const float2* src = a.inH + hrow_base(valid ? g : 0, M, a.logT);
+#pragma unroll
+    for (int q = 0; q < P; ++q)
+      v[q] = valid ? __ldcg(src + ((int64_t)(tau + TPT * q) << a.logT)) : make_float2(0.f, 0.f);
+    fft_core<P, +1>(v, sm, tau, c, C, M, a.logM, a.twM, a.tws, nthr);
+    if (valid) {
+      float2* o = reinterpret_cast<float2*>(a.outR + g * N);
+#pragma unroll
+      for (int q = 0; q < P; ++q) o[tau + TPT * q] = v[q];
+    }
+    return;
+  } else if constexpr (MODE == ROW_C2R) {
+    // ROW_NOISE_H (d = 1, one row per field): stage X[0..M] of every row of
+    // the CTA in shared memory, then split into Z.
     const uint64_t key = a.g.seed + (uint64_t)(a.g.field0 + field);
     float2 xm = make_float2(0.f, 0.f);
     if (valid) {
-      if constexpr (SRC == ROW_LOAD_H) {
-        const float2* src = a.inH + hb;
 #pragma unroll
-        for (int q = 0; q < P; ++q) v[q] = __ldcg(src + ((int64_t)(tau + TPT * q) << a.logT));
-        if (tau == 0) xm = __ldcg(src + ((int64_t)M << a.logT));
-      } else {  // ROW_NOISE_H: d = 1, one row per field
-#pragma unroll
-        for (int q = 0; q < P; ++q) {
-          const int k = tau + TPT * q;
-          v[q] = cscale(alg2_xi_1d(k, M, key, a.g.trig), __ldg(a.g.stab + k));
-        }
-        if (tau == 0) xm = cscale(alg2_xi_1d(M, M, key, a.g.trig), __ldg(a.g.stab + M));
+      for (int q = 0; q < P; ++q) {
+        const int k = tau + TPT * q;
+        v[q] = cscale(alg2_xi_1d(k, M, key, a.g.trig), __ldg(a.g.stab + k));
       }
+      if (tau == 0) xm = cscale(alg2_xi_1d(M, M, key, a.g.trig), __ldg(a.g.stab + M));
     } else {
 #pragma unroll
       for (int q = 0; q < P; ++q) v[q] = make_float2(0.f, 0.f);

@@ -19,18 +19,16 @@
 
 namespace grf {
 
-// Threads per CTA of each radix: 256 for radix 16 (3 CTAs per SM), 512 for
-// radix 8 (N = 4096 needs 512 threads of 8 points), 1024 for radix 4 and below.
-template <int P>
-constexpr int kMaxThreads = P >= 16 ? 256 : (P == 8 ? 512 : 1024);
-template <int P>
-constexpr int kMinBlocks = P >= 16 ? 3 : (P == 8 ? 2 : 1);
 
-template <int P, int SRC, int MODE>
+template <int P, int SRC, int MODE, int PAIR>
 __global__ void __launch_bounds__(kMaxThreads<P>, kMinBlocks<P>) col_kernel(ColArgs a) {
   extern __shared__ float2 sm[];
-  const int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-  col_body<P, SRC, MODE>(a, blockIdx.x, blockIdx.y, blockIdx.z, blk, blockDim.x, sm);
+  if constexpr (PAIR) {
+    col_body_pair<P, SRC, MODE>(a, CtaCoordsHW{}, blockDim.x, sm);
+  } else {
+    const int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    col_body<P, SRC, MODE>(a, blockIdx.x, blockIdx.y, blockIdx.z, blk, blockDim.x, sm);
+  }
 }
 
 template <int P, int SRC, int MODE>
@@ -42,14 +40,15 @@ __global__ void __launch_bounds__(kMaxThreads<P>, kMinBlocks<P>) row_kernel(RowA
 // Grid-stride forms of the two 2-D/3-D passes: `gridDim.x` CTAs walk all
 // tiles, so a small grid leaves room on every SM for another kernel's CTAs
 // (the pipelined schedule runs one CTA per SM of each pass side by side).
-template <int P, int SRC, int MODE>
+template <int P, int SRC, int MODE, int PAIR>
 __global__ void __launch_bounds__(512) col_kernel_gs(ColArgs a, int gx, int gy, int gz) {
   extern __shared__ float2 sm[];
   const int64_t n = (int64_t)gx * gy * gz;
   for (int64_t t = blockIdx.x; t < n; t += gridDim.x) {
     const int bx = (int)(t % gx);
     const int64_t r = t / gx;
-    col_body<P, SRC, MODE>(a, bx, (int)(r % gy), r / gy, t, blockDim.x, sm);
+    if constexpr (PAIR) col_body_pair<P, SRC, MODE>(a, CtaCoordsVal{bx, (int)(r % gy), r / gy}, blockDim.x, sm);
+    else col_body<P, SRC, MODE>(a, bx, (int)(r % gy), r / gy, t, blockDim.x, sm);
     __syncthreads();
   }
 }
@@ -80,6 +79,9 @@ __global__ void __launch_bounds__(512) fourstep_stage2(FourStepArgs a) {
 // ---------------------------------------------------------------------------
 
 int points_per_thread(int n) { return n >= 16 ? 16 : n; }
+
+// Pair mode adds one stash slot per point of the CTA (C N entries).
+size_t col_pair_smem_bytes(int N, int C) { return col_smem_bytes(N, C) + (size_t)C * N * sizeof(float2); }
 
 size_t col_smem_bytes(int N, int C) {
   size_t e = (size_t)spad_h(N) * C * sizeof(float2);
@@ -135,29 +137,35 @@ cudaError_t prepare_kernel(const void* k, int threads, size_t smem) {
   return cudaSuccess;
 }
 
-template <int P, int SRC, int MODE>
+template <int P, int SRC, int MODE, int PAIR>
 static cudaError_t launch_col_t(const ColArgs& a, dim3 grid, cudaStream_t s) {
   const int threads = a.C * a.N / P;
-  const size_t smem = col_smem_bytes(a.N, a.C);
-  auto k = col_kernel<P, SRC, MODE>;
+  const size_t smem = PAIR ? col_pair_smem_bytes(a.N, a.C) : col_smem_bytes(a.N, a.C);
+  auto k = col_kernel<P, SRC, MODE, PAIR>;
   cudaError_t e = prepare_kernel((const void*)k, threads, smem);
   if (e != cudaSuccess) return e;
   k<<<grid, threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int SRC, int MODE>
+template <int SRC, int MODE, int PAIR = 0>
 static cudaError_t launch_col_p(int P, const ColArgs& a, dim3 grid, cudaStream_t s) {
   switch (P) {
-    case 2: return launch_col_t<2, SRC, MODE>(a, grid, s);
-    case 4: return launch_col_t<4, SRC, MODE>(a, grid, s);
-    case 8: return launch_col_t<8, SRC, MODE>(a, grid, s);
-    case 16: return launch_col_t<16, SRC, MODE>(a, grid, s);
+    case 2: return launch_col_t<2, SRC, MODE, PAIR>(a, grid, s);
+    case 4: return launch_col_t<4, SRC, MODE, PAIR>(a, grid, s);
+    case 8: return launch_col_t<8, SRC, MODE, PAIR>(a, grid, s);
+    case 16: return launch_col_t<16, SRC, MODE, PAIR>(a, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_col(int src, int mode, int P, const ColArgs& a, dim3 grid, cudaStream_t s) {
+  if (a.zpair) {  // the inverse passes that end before the c2r pass
+    if (src == COL_NOISE && mode == COL_INV) return launch_col_p<COL_NOISE, COL_INV, 1>(P, a, grid, s);
+    if (src == COL_LOAD && mode == COL_INV) return launch_col_p<COL_LOAD, COL_INV, 1>(P, a, grid, s);
+    if (src == COL_LOAD && mode == COL_FWD_SCALE_INV) return launch_col_p<COL_LOAD, COL_FWD_SCALE_INV, 1>(P, a, grid, s);
+    return cudaErrorInvalidValue;
+  }
   if (src == COL_NOISE && mode == COL_INV) return launch_col_p<COL_NOISE, COL_INV>(P, a, grid, s);
   if (src == COL_LOAD && mode == COL_INV) return launch_col_p<COL_LOAD, COL_INV>(P, a, grid, s);
   if (src == COL_LOAD && mode == COL_FWD) return launch_col_p<COL_LOAD, COL_FWD>(P, a, grid, s);
@@ -226,15 +234,15 @@ static cudaError_t launch_gs_t(int which, const ColArgs* ca, const RowArgs* ra, 
                                cudaStream_t s) {
   if (which == 0) {
     const int threads = ca->C * ca->N / P;
-    const size_t smem = col_smem_bytes(ca->N, ca->C);
-    auto k = col_kernel_gs<P, COL_NOISE, COL_INV>;
+    const size_t smem = ca->zpair ? col_pair_smem_bytes(ca->N, ca->C) : col_smem_bytes(ca->N, ca->C);
+    auto k = ca->zpair ? col_kernel_gs<P, COL_NOISE, COL_INV, 1> : col_kernel_gs<P, COL_NOISE, COL_INV, 0>;
     cudaError_t e = prepare_kernel((const void*)k, threads, smem);
     if (e != cudaSuccess) return e;
     k<<<ctas, threads, smem, s>>>(*ca, tiles.x, tiles.y, tiles.z);
   } else {
     const int threads = ra->C * (ra->M / P);
     const size_t smem = row_smem_bytes(ra->M, ra->C);
-    auto k = row_kernel_gs<P, ROW_LOAD_H, ROW_C2R>;
+    auto k = row_kernel_gs<P, ROW_LOAD_Z, ROW_C2R>;
     cudaError_t e = prepare_kernel((const void*)k, threads, smem);
     if (e != cudaSuccess) return e;
     k<<<ctas, threads, smem, s>>>(*ra, (int64_t)tiles.x);
@@ -265,7 +273,7 @@ cudaError_t launch_row_c2r_gs(int P, const RowArgs& a, int64_t ntiles, int ctas,
 }
 
 cudaError_t launch_row(int src, int mode, int P, const RowArgs& a, dim3 grid, cudaStream_t s) {
-  if (src == ROW_LOAD_H && mode == ROW_C2R) return launch_row_p<ROW_LOAD_H, ROW_C2R>(P, a, grid, s);
+  if (src == ROW_LOAD_Z && mode == ROW_C2R) return launch_row_p<ROW_LOAD_Z, ROW_C2R>(P, a, grid, s);
   if (src == ROW_NOISE_H && mode == ROW_C2R) return launch_row_p<ROW_NOISE_H, ROW_C2R>(P, a, grid, s);
   if (src == ROW_LOAD_REAL && mode == ROW_R2C) return launch_row_p<ROW_LOAD_REAL, ROW_R2C>(P, a, grid, s);
   if (src == ROW_NOISE_REAL && mode == ROW_R2C) return launch_row_p<ROW_NOISE_REAL, ROW_R2C>(P, a, grid, s);

@@ -15,9 +15,12 @@ enum ColMode {
 };
 
 // Sources and modes of the row pass (the contiguous last axis).
-enum RowSrc { ROW_LOAD_H = 0, ROW_NOISE_H = 1, ROW_LOAD_REAL = 2, ROW_NOISE_REAL = 3 };
+//   ROW_LOAD_Z: Z[k] = (X[k] + conj X[M-k]) + i e^{2 pi i k/N} (X[k] - conj X[M-k]),
+//   k < M, as the last column pass leaves it (pair mode) in the half-spectrum
+//   layout; ROW_NOISE_H: X drawn in the row (1-D).
+enum RowSrc { ROW_LOAD_Z = 0, ROW_NOISE_H = 1, ROW_LOAD_REAL = 2, ROW_NOISE_REAL = 3 };
 enum RowMode {
-  ROW_C2R = 0,            // half spectrum (M+1) -> N = 2M reals
+  ROW_C2R = 0,            // half spectrum (M+1) -> N = 2M reals: z = IFFT_M(Z), f[2m] + i f[2m+1] = z[m]
   ROW_R2C = 1,            // N reals -> half spectrum (M+1), forward
   ROW_R2C_SCALE_C2R = 2,  // 1-D Algorithm 1 in one pass
   ROW_R2C_ADJ = 3         // 1-D adjoint: forward r2c, then reduce against regenerated xi
@@ -50,6 +53,9 @@ struct ColArgs {
   const float2* tw;   // tw[k] = exp(2 pi i k / N)
   const float2* tws;  // radix-16 stage tables (see fft_core)
   int plane_is_k1;   // COL_NOISE / scale / adjoint: the transform axis is axis 1
+  int zpair;         // COL_INV / COL_FWD_SCALE_INV on a plane of M+1 columns: slot p takes
+                     // columns p and M - p and writes Z of the c2r split (see col_body)
+  const float2* twz; // zpair: exp(2 pi i k / N_d), k <= M/2
   HalfGeom g;
   double* partial;   // COL_FWD_ADJ: 3 doubles per CTA, indexed by linear block id
 };
@@ -105,6 +111,22 @@ cudaError_t launch_row(int src, int mode, int P, const RowArgs& a, dim3 grid, cu
 cudaError_t launch_col_noise_gs(int P, const ColArgs& a, dim3 tiles, int ctas, cudaStream_t s);
 cudaError_t launch_row_c2r_gs(int P, const RowArgs& a, int64_t ntiles, int ctas, cudaStream_t s);
 size_t col_smem_bytes(int N, int C);
+size_t col_pair_smem_bytes(int N, int C);  // pair mode (ColArgs::zpair)
+// The c2r pass as a persistent kernel fed by bulk asynchronous copies
+// (c2r_tma.cu): groups of C rows (C a power of two >= 2, the workspace tile T
+// dividing C, nrows a multiple of C), two shared-memory slots per CTA.  At most
+// ctas_per_sm CTAs per SM (0: as many as fit).  A wait that times out stores
+// GRF_ERR_TIMEOUT in *status.
+bool c2r_tma_ok(const RowArgs& a);
+size_t c2r_tma_slot_bytes(int M, int C);
+cudaError_t launch_row_c2r_tma(int P, const RowArgs& a, int ctas_per_sm, int num_sms, int* status, cudaStream_t s);
+// Launch bounds of the transform kernels: 256 threads per CTA for radix 16
+// (3 CTAs per SM), 512 for radix 8 (N = 4096 needs 512 threads of 8 points),
+// 1024 for radix 4 and below.
+template <int P>
+constexpr int kMaxThreads = P >= 16 ? 256 : (P == 8 ? 512 : 1024);
+template <int P>
+constexpr int kMinBlocks = P >= 16 ? 3 : (P == 8 ? 2 : 1);
 // Dynamic shared memory and the L1/shared carveout of a kernel for a launch shape.
 cudaError_t prepare_kernel(const void* k, int threads, size_t smem);
 size_t row_smem_bytes(int M, int C);

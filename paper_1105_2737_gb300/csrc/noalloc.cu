@@ -159,8 +159,10 @@ extern "C" grf_status grf_sample_2d_static(const int64_t* n, const double* L, co
   ColArgs a{};
   a.N = N1;
   a.logN = lg2(N1);
-  a.C = cols_per_cta(N1, M + 1);
+  a.C = cols_per_cta(N1, M / 2 + 1);
   a.ncols = M + 1;
+  a.zpair = 1;  // pairs of columns (p, M - p): the pass writes Z of the c2r split
+  a.twz = tw + N2;
   a.T = 1;
   a.logT = 0;
   a.bstride = (int64_t)N1 * (M + 1);
@@ -179,7 +181,7 @@ extern "C" grf_status grf_sample_2d_static(const int64_t* n, const double* L, co
   r.twM = tw + M;
   r.twN = tw + 2 * M;
   r.tws = tw + 2 * maxlen;
-  const dim3 gc((unsigned)((a.ncols + a.C - 1) / a.C), 1, 1);
+  const dim3 gc((unsigned)((M / 2 + 1 + a.C - 1) / a.C), 1, 1);
   const dim3 gr((unsigned)((r.nrows + r.C - 1) / r.C));
   // One field at a time through the one-field half-spectrum slot; the stream
   // orders the reuse of the slot between consecutive fields.
@@ -189,7 +191,7 @@ extern "C" grf_status grf_sample_2d_static(const int64_t* n, const double* L, co
     r.g = a.g;
     r.outR = out + b * (int64_t)N1 * N2;
     if (launch_col(COL_NOISE, COL_INV, points_per_thread(N1), a, gc, s) != cudaSuccess ||
-        launch_row(ROW_LOAD_H, ROW_C2R, M >= 16 ? 16 : M, r, gr, s) != cudaSuccess)
+        launch_row(ROW_LOAD_Z, ROW_C2R, M >= 16 ? 16 : M, r, gr, s) != cudaSuccess)
       return reject(GRF_ERR_CUDA, "grf_sample_2d_static: kernel launch failed");
   }
   return GRF_OK;

@@ -26,9 +26,12 @@ def _key2(shape, alg, max_batch):
     return "plan|%s|%d" % (gpu, len(shape)) + "".join("x%d" % v for v in n) + "|alg%d|b%d" % (alg, max_batch)
 
 
-# (T, colA.P, colA.C, colB.P, colB.C, row.P, row.C, pipe)
+# (T, colA.P, colA.C, colB.P, colB.C, row.P, row.C, pipe[, row_tma])
 SCHEDS_2D = [(1, 16, 1, 16, 1, 16, 1, 1), (8, 8, 2, 16, 1, 8, 4, 1), (4, 4, 4, 16, 1, 4, 8, 2),
-             (16, 16, 4, 16, 1, 16, 2, 4), (2, 8, 1, 16, 1, 4, 1, 1)]
+             (16, 16, 4, 16, 1, 16, 2, 4), (2, 8, 1, 16, 1, 4, 1, 1),
+             # c2r pass fed by bulk copies: tile T = C, T < C, T = 1, pipelined
+             (2, 16, 1, 16, 1, 16, 2, 1, 1), (4, 8, 2, 16, 1, 8, 8, 1, 1), (1, 16, 1, 16, 1, 4, 4, 1, 1),
+             (16, 16, 4, 16, 1, 16, 16, 2, 1), (8, 16, 2, 16, 1, 16, 8, 4, 1)]
 
 
 @pytest.mark.parametrize("sched", SCHEDS_2D)
@@ -45,13 +48,15 @@ def test_forced_schedules_2d(sched, tmp_path):
     sch = g.schedule
     assert (sch["T"], sch["colA_P"], sch["colA_C"], sch["row_P"], sch["row_C"], sch["pipe"]) == \
         (sched[0], sched[1], sched[2], sched[5], sched[6], sched[7])
+    assert sch["row_tma"] == (sched[8] if len(sched) > 8 else 0)
     f = g.sample(seed=4, batch=batch).cpu().numpy()
     ref = O.sample(shape, Lb, O.Spectrum(O.MATERN, 1.0, 0.05, 1.5), 4, batch)
     rel = np.linalg.norm(f - ref) / np.linalg.norm(ref)
     assert rel <= 2e-6 and np.abs(f - ref).max() <= 1e-5, rel
 
 
-@pytest.mark.parametrize("sched", [(1, 8, 4, 4, 8, 8, 4, 1), (1, 4, 2, 8, 2, 16, 4, 2)])
+@pytest.mark.parametrize("sched", [(1, 8, 4, 4, 8, 8, 4, 1), (1, 4, 2, 8, 2, 16, 4, 2),
+                                   (1, 8, 4, 4, 8, 16, 4, 1, 1), (1, 16, 1, 16, 1, 8, 8, 2, 1)])
 def test_forced_schedules_3d(sched, tmp_path):
     from paper_1105_2737_gb300 import api
     shape, Lb, batch = (32, 64, 64), (1.0, 1.0, 1.0), 2
@@ -87,3 +92,25 @@ def test_tune_picks_a_valid_schedule(tmp_path):
     f = g2.sample(seed=1, batch=2).cpu().numpy()
     ref = O.sample((512, 512), (1.0, 1.0), O.Spectrum(O.MATERN, 1.0, 0.05, 2.5), 1, 2)
     assert np.linalg.norm(f - ref) / np.linalg.norm(ref) <= 2e-6
+
+
+def test_bulk_copy_c2r_falls_back_below_one_group(tmp_path):
+    """A bulk-copy schedule whose row group (C = 8 rows) is larger than the rows
+    of the call (one 4 x 8 field: 4 rows) runs the plain row kernel instead and
+    still gives the oracle's field; the full batch takes the bulk-copy kernel."""
+    from paper_1105_2737_gb300 import api
+    shape, Lb = (4, 8), (1.0, 1.0)
+    sched = (4, 4, 1, 16, 1, 4, 8, 1, 1)
+    path = tmp_path / "tune.txt"
+    path.write_text(_key2(shape, 2, 2) + " " + " ".join(str(v) for v in sched) + "\n")
+    os.environ["GRF_TUNE_CACHE"] = str(path)
+    try:
+        g = api.GRF(shape, Lb, ell=0.2, nu=1.5, max_batch=2)
+    finally:
+        del os.environ["GRF_TUNE_CACHE"]
+    assert g.schedule["row_tma"] == 1 and g.schedule["row_C"] == 8
+    spec = O.Spectrum(O.MATERN, 1.0, 0.2, 1.5)
+    for batch in (1, 2):
+        f = g.sample(seed=9, batch=batch).cpu().numpy()
+        ref = O.sample(shape, Lb, spec, 9, batch)
+        assert np.abs(f - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
