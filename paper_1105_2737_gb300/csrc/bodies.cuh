@@ -84,11 +84,13 @@ GRF_DEV void alg2_column_normals(float2 (&v)[P], int tau, int TPT, int C, int km
     }
   } else if (C < 32) {
     const bool odd = (tau & 1) != 0;
+    // row k1 = tau + TPT qa has call ((k1 >> 1) Nmid + kmid)(M + 1) + kd; with TPT
+    // even, k1 >> 1 = (tau >> 1) + (TPT / 2) qa, so the calls step by a constant
+    const uint64_t stride = (uint64_t)(TPT >> 1) * (uint64_t)g.Nmid * (uint64_t)(g.M + 1);
+    uint64_t call = alg2_call_index(tau + (odd ? TPT * (P / 2) : 0), kmid, kd, g.Nmid, g.M);
 #pragma unroll
-    for (int i = 0; i < P / 2; ++i) {
-      const int qa = odd ? i + P / 2 : i;  // this lane draws the call of its row qa
-      const int k1 = tau + TPT * qa;
-      const u32x4 w = philox_call(alg2_call_index(k1, kmid, kd, g.Nmid, g.M), 0u, key);
+    for (int i = 0; i < P / 2; ++i, call += stride) {  // this lane draws the call of its row qa
+      const u32x4 w = philox_call(call, 0u, key);
       const uint32_t oa = odd ? w.z : w.x, ob = odd ? w.w : w.y;
       const uint32_t pa = odd ? w.x : w.z, pb = odd ? w.y : w.w;
       const uint32_t ra = __shfl_xor_sync(0xffffffffu, pa, C);

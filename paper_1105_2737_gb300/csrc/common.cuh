@@ -66,9 +66,11 @@ GRF_DEV u32x4 philox_call(uint64_t q, uint32_t tag, uint64_t key) {
                        (uint32_t)(key >> 32));
 }
 
-// u = (2 (x >> 9) + 1) 2^-24: exact in FP32, in (0, 1).
+// u = (2 (x >> 9) + 1) 2^-24: exact in FP32, in (0, 1).  Formed from the bits:
+// the float with exponent 0 and mantissa x >> 9 is 1 + (x >> 9) 2^-23, and adding
+// 2^-24 - 1 (exact in FP32) gives u, which is representable, so the add is exact.
 GRF_DEV float uniform_open(uint32_t x) {
-  return (float)((x >> 9) * 2u + 1u) * 5.9604644775390625e-8f;
+  return __int_as_float(0x3F800000u | (x >> 9)) + (-0.999999940395355224609375f);
 }
 GRF_DEV double uniform_open_d(uint32_t x) {
   return (double)((x >> 9) * 2u + 1u) * 5.9604644775390625e-8;
@@ -85,9 +87,12 @@ GRF_DEV float2 box_muller(uint32_t wa, uint32_t wb, const float2* __restrict__ t
   const float ua = uniform_open(wa);
   const float rho2 = -2.0f * logf(ua);
   const float rho = rho2 * rsqrtf(rho2);
-  const uint32_t m = (wb >> 9) * 2u + 1u;
-  const float2 t = __ldg(trig + (m >> 16));
-  const float dl = (float)(m & 0xFFFFu) * 3.7450703e-7f;  // 2 pi / 2^24
+  // m' >> 16 = wb >> 24; m' & 0xFFFF = 2 r + 1 with r = (wb >> 9) & 0x7FFF, and
+  // (2 r + 1) 2^-16 is formed exactly from the bits as in uniform_open, then
+  // scaled by 2 pi / 2^8 (the same product as (2 r + 1) times 2 pi / 2^24)
+  const float2 t = __ldg(trig + (wb >> 24));
+  const float dl = (__int_as_float(0x3F800000u | ((wb >> 1) & 0x007FFF00u)) + (-0.9999847412109375f)) *
+                   0.024543692606170259f;  // 2 pi / 2^8
   const float d2 = dl * dl;
   const float cd = fmaf(d2, fmaf(d2, 1.0f / 24.0f, -0.5f), 1.0f);
   const float sd = dl * fmaf(d2, fmaf(d2, 1.0f / 120.0f, -1.0f / 6.0f), 1.0f);
