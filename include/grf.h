@@ -136,9 +136,11 @@ grf_status grf_plan_set_spectrum(grf_plan p, const grf_spectrum* spec, void* str
  * pipelining depth, by coordinate descent with CUDA events on `stream`.  The
  * winner is applied and stored in the tuning cache (GRF_TUNE_CACHE, default
  * $HOME/.cache/grf_gb300_tune.txt) under the GPU name, grid, algorithm and
- * max_batch; later grf_plan_create calls for the same key apply it.  Setting
- * GRF_TUNE=1 makes grf_plan_create tune.  FP32 2-D and 3-D plans.  Allocates a
- * temporary output of at most 64 MiB (or one field) while it runs.
+ * max_batch; later grf_plan_create calls for the same key apply it, and
+ * grf_plan_tune on such a plan keeps that schedule and returns GRF_OK without
+ * timing (GRF_TUNE_FORCE=1 times again).  Setting GRF_TUNE=1 makes
+ * grf_plan_create tune.  FP32 2-D and 3-D plans.  Allocates a temporary output
+ * of at most 64 MiB (or one field) while it runs.
  */
 grf_status grf_plan_tune(grf_plan p, void* stream);
 

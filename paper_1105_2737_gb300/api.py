@@ -65,7 +65,9 @@ class GRF:
         return torch.empty((batch,) + self.shape, dtype=self.dtype, device=self.device)
 
     def tune(self) -> dict:
-        """Time the candidate schedules (radix, tiles, pipelining) and keep the best."""
+        """Time the candidate schedules (radix, tiles, pipelining) and keep the best.
+        A schedule this plan took from the tuning cache is kept as it is
+        (GRF_TUNE_FORCE=1 times again)."""
         with torch.cuda.device(self.device):
             L.grf_plan_tune(self.handle, _stream_ptr(self.device))
         return self.schedule

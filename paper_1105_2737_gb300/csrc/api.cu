@@ -157,6 +157,7 @@ struct grf_plan_s {
   // caller's stream, the others on tail_stream
   int pipe = 1;
   int row_tma = 0;  // c2r pass: 0 = row kernel, 1 = persistent kernel fed by bulk async copies
+  bool sched_cached = false;  // the schedule came from the tuning cache at creation
   int gs_ctas = 1;  // grid-stride CTAs per SM of each pass when pipelined (0: full grids)
   int num_sms = 0;
   cudaStream_t tail_stream = nullptr;
@@ -416,10 +417,10 @@ bool valid_sched(const ColSched& c, int N, int64_t ncols, bool rows) {
 // Values: T, colA.P, colA.C, colB.P, colB.C, row.P, row.C, pipe, row_tma
 // (absent: 0).  Applied only if every entry is a schedule this plan could have
 // chosen itself.
-void apply_schedule(grf_plan_s* p, const std::vector<int>& v) {
-  if ((v.size() != 8 && v.size() != 9) || p->d < 2) return;
+bool apply_schedule(grf_plan_s* p, const std::vector<int>& v) {
+  if ((v.size() != 8 && v.size() != 9) || p->d < 2) return false;
   const int tma = v.size() == 9 ? v[8] : 0;
-  if (tma < 0 || tma > 1) return;
+  if (tma < 0 || tma > 1) return false;
   ColSched a, b, r;
   a.P = v[1];
   a.C = v[2];
@@ -428,11 +429,11 @@ void apply_schedule(grf_plan_s* p, const std::vector<int>& v) {
   r.P = v[5];
   r.C = v[6];
   const int T = v[0];
-  if (T < 1 || (T & (T - 1)) || p->N1 % T || (p->d == 3 && T != 1)) return;
-  if (!valid_sched(a, p->N1, (int64_t)p->Nmid * (p->M + 1), false)) return;
-  if (p->d == 3 && !valid_sched(b, p->Nmid, p->M + 1, false)) return;
-  if (!valid_sched(r, p->M, p->max_batch * (p->ntot / p->n[p->d - 1]), true)) return;
-  if (v[7] < 1 || v[7] > 8) return;
+  if (T < 1 || (T & (T - 1)) || p->N1 % T || (p->d == 3 && T != 1)) return false;
+  if (!valid_sched(a, p->N1, (int64_t)p->Nmid * (p->M + 1), false)) return false;
+  if (p->d == 3 && !valid_sched(b, p->Nmid, p->M + 1, false)) return false;
+  if (!valid_sched(r, p->M, p->max_batch * (p->ntot / p->n[p->d - 1]), true)) return false;
+  if (v[7] < 1 || v[7] > 8) return false;
   p->T = T;
   p->colA = a;
   if (p->d == 3) p->colB = b;
@@ -440,6 +441,7 @@ void apply_schedule(grf_plan_s* p, const std::vector<int>& v) {
   p->row.C = r.C;
   p->pipe = v[7];
   p->row_tma = tma;
+  return true;
 }
 
 // A launch bracketed by timing events when the plan records them.
@@ -677,7 +679,7 @@ grf_status grf_plan_create(grf_plan* out, int d, const int64_t* n, const double*
       PLAN_CUDA(dmalloc(&p->ws, (size_t)(p->chunk * p->hsize)), "workspace");
       {  // a tuned schedule for this GPU and problem, if one was stored
         std::vector<int> v;
-        if (tune_cache_lookup(plan_key(p), &v)) apply_schedule(p, v);
+        if (tune_cache_lookup(plan_key(p), &v)) p->sched_cached = apply_schedule(p, v);
       }
       if (const char* pe = std::getenv("GRF_PIPELINE")) p->pipe = std::max(1, std::min(8, std::atoi(pe)));
       if (const char* ge = std::getenv("GRF_GS_CTAS")) p->gs_ctas = std::max(0, std::min(8, std::atoi(ge)));
@@ -776,6 +778,8 @@ grf_status grf_plan_tune(grf_plan p, void* stream) {
   if (st != GRF_OK) return st;
   if (p->kind != 0 || p->prec != GRF_FP32 || p->d < 2)
     return fail(GRF_ERR_UNSUPPORTED, "the tuner covers FP32 2-D and 3-D plans");
+  const char* force = std::getenv("GRF_TUNE_FORCE");
+  if (p->sched_cached && !(force && force[0] == '1')) return GRF_OK;  // already tuned on this GPU
   cudaStream_t s = (cudaStream_t)stream;
   // enough fields for a few waves of CTAs, within max_batch
   int64_t bt = (int64_t)((64ll << 20) / p->ntot);

@@ -114,3 +114,22 @@ def test_bulk_copy_c2r_falls_back_below_one_group(tmp_path):
         f = g.sample(seed=9, batch=batch).cpu().numpy()
         ref = O.sample(shape, Lb, spec, 9, batch)
         assert np.abs(f - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
+
+
+def test_tune_keeps_a_cached_schedule(tmp_path):
+    """A plan whose schedule came from the tuning cache keeps it when tuned
+    again (no re-timing), unless GRF_TUNE_FORCE=1."""
+    from paper_1105_2737_gb300 import api
+    shape, Lb, batch = (256, 512), (1.0, 1.0), 3
+    sched = (8, 8, 2, 16, 1, 8, 4, 1)
+    path = tmp_path / "tune.txt"
+    path.write_text(_key2(shape, 2, batch) + " " + " ".join(str(v) for v in sched) + "\n")
+    os.environ["GRF_TUNE_CACHE"] = str(path)
+    try:
+        g = api.GRF(shape, Lb, ell=0.05, nu=1.5, max_batch=batch)
+        before = dict(g.schedule)
+        after = g.tune()
+        assert after == before and (after["T"], after["colA_P"], after["row_C"]) == (8, 8, 4)
+        assert path.read_text().count("\n") == 1  # nothing re-timed or stored
+    finally:
+        del os.environ["GRF_TUNE_CACHE"]
