@@ -67,6 +67,21 @@ GRF_DEV void block_sum3(double v0, double v1, double v2, double* out3, double* s
   }
 }
 
+// xi_K on a plane kd in {0, M} (Eq. conj): the member of {K, -K} with the larger
+// row-major index keeps its normals, the other takes their conjugate, and a
+// self-conjugate K takes z_re.  Out of line: the column pass needs it for two
+// columns only, and inlined copies would crowd the registers of the others.
+static __device__ __noinline__ float2 plane_xi(int k1, int kmid, int kd, int N1, int Nmid, int M, uint64_t key,
+                                               const float2* trig) {
+  const int nk1 = (N1 - k1) & (N1 - 1), nkm = (Nmid - kmid) & (Nmid - 1);
+  const int row = k1 * Nmid + kmid, nrow = nk1 * Nmid + nkm;
+  const bool own = row >= nrow;
+  const float2 z = alg2_normals_grid(own ? k1 : nk1, own ? kmid : nkm, kd, Nmid, M, key, trig);
+  if (row == nrow) return make_float2(z.x, 0.f);
+  const float r2 = 0.70710678118654752440f;
+  return make_float2(z.x * r2, own ? z.y * r2 : -z.y * r2);
+}
+
 // Normals (z_re, z_im) of Algorithm 2 for the entries (k1 = tau + TPT q, kmid, kd)
 // of this thread.  Rows k1 = 2i and 2i + 1 share one Philox call (words 0,1 and
 // 2,3).  With TPT even they sit on threads tau and tau ^ 1 (lanes t and t ^ C):
@@ -142,22 +157,11 @@ GRF_DEV void col_transform(const ColArgs& a, int col, bool valid, int64_t field,
 #pragma unroll
       for (int q = 0; q < P; ++q) v[q] = cscale(v[q], s[q] * r2);
     } else {
-      // planes kd in {0, M}: conjugate pairs (Eq. conj) and the self-conjugate points
-      const int nkm = (g.Nmid - cg.kmid) & (g.Nmid - 1);
+      // planes kd in {0, M}: conjugate pairs (Eq. conj) and the self-conjugate
+      // points, out of line (2 of the M + 1 columns take this branch)
 #pragma unroll
-      for (int q = 0; q < P; ++q) {
-        const int k1 = tau + TPT * q;
-        const int nk1 = (g.N1 - k1) & (g.N1 - 1);
-        const int row = k1 * g.Nmid + cg.kmid, nrow = nk1 * g.Nmid + nkm;
-        float2 xi = make_float2(v[q].x * r2, v[q].y * r2);
-        if (row == nrow) {
-          xi = make_float2(v[q].x, 0.f);
-        } else if (row < nrow) {  // the partner -K carries the pair's normals
-          const float2 z = alg2_normals_grid(nk1, nkm, cg.kd, g.Nmid, g.M, key, g.trig);
-          xi = make_float2(z.x * r2, -z.y * r2);
-        }
-        v[q] = cscale(xi, s[q]);
-      }
+      for (int q = 0; q < P; ++q)
+        v[q] = cscale(plane_xi(tau + TPT * q, cg.kmid, cg.kd, g.N1, g.Nmid, g.M, key, g.trig), s[q]);
     }
     if (!valid) {
 #pragma unroll
