@@ -84,40 +84,63 @@ static __device__ __noinline__ float2 plane_xi(int k1, int kmid, int kd, int N1,
 
 // Normals (z_re, z_im) of Algorithm 2 for the entries (k1 = tau + TPT q, kmid, kd)
 // of this thread.  Rows k1 = 2i and 2i + 1 share one Philox call (words 0,1 and
-// 2,3).  With TPT even they sit on threads tau and tau ^ 1 (lanes t and t ^ C):
-// each draws the call for half of its rows and passes the partner its words.
-// With TPT == 1 both rows are this thread's (q and q ^ 1).
+// 2,3).  Three ways to deal the words out, by the thread layout:
+//   NV_INTHREAD (TPT == 1): both rows of a call are this thread's (q and q ^ 1);
+//   NV_SHFL (TPT even, C < 32): they sit on threads tau and tau ^ 1 (lanes t and
+//     t ^ C); each lane draws the call for half of its rows and passes the
+//     partner its words;
+//   NV_PLAIN: every entry draws its own call (lanes t and t ^ C in other warps).
+// NV_ANY picks one at run time; the per-pass kernels are compiled for one
+// variant each, so that the code of the others does not crowd their registers.
 template <int P>
+GRF_DEV void normals_inthread(float2 (&v)[P], int kmid, int kd, const HalfGeom& g, uint64_t key) {
+#pragma unroll
+  for (int i = 0; i < P / 2; ++i) {
+    const u32x4 w = philox_call(alg2_call_index(2 * i, kmid, kd, g.Nmid, g.M), 0u, key);
+    v[2 * i] = box_muller(w.x, w.y, g.trig);
+    v[2 * i + 1] = box_muller(w.z, w.w, g.trig);
+  }
+}
+template <int P>
+GRF_DEV void normals_shfl(float2 (&v)[P], int tau, int TPT, int C, int kmid, int kd, const HalfGeom& g,
+                          uint64_t key) {
+  const bool odd = (tau & 1) != 0;
+  // row k1 = tau + TPT qa has call ((k1 >> 1) Nmid + kmid)(M + 1) + kd; with TPT
+  // even, k1 >> 1 = (tau >> 1) + (TPT / 2) qa, so the calls step by a constant
+  const uint64_t stride = (uint64_t)(TPT >> 1) * (uint64_t)g.Nmid * (uint64_t)(g.M + 1);
+  uint64_t call = alg2_call_index(tau + (odd ? TPT * (P / 2) : 0), kmid, kd, g.Nmid, g.M);
+#pragma unroll
+  for (int i = 0; i < P / 2; ++i, call += stride) {  // this lane draws the call of its row qa
+    const u32x4 w = philox_call(call, 0u, key);
+    const uint32_t oa = odd ? w.z : w.x, ob = odd ? w.w : w.y;
+    const uint32_t pa = odd ? w.x : w.z, pb = odd ? w.y : w.w;
+    const uint32_t ra = __shfl_xor_sync(0xffffffffu, pa, C);
+    const uint32_t rb = __shfl_xor_sync(0xffffffffu, pb, C);
+    const float2 zo = box_muller(oa, ob, g.trig);  // own row qa
+    const float2 zr = box_muller(ra, rb, g.trig);  // own row qb, drawn by the partner
+    v[i] = odd ? zr : zo;
+    v[i + P / 2] = odd ? zo : zr;
+  }
+}
+template <int P>
+GRF_DEV void normals_plain(float2 (&v)[P], int tau, int TPT, int kmid, int kd, const HalfGeom& g, uint64_t key) {
+#pragma unroll
+  for (int q = 0; q < P; ++q) v[q] = alg2_normals_grid(tau + TPT * q, kmid, kd, g.Nmid, g.M, key, g.trig);
+}
+
+template <int P, int NV = NV_ANY>
 GRF_DEV void alg2_column_normals(float2 (&v)[P], int tau, int TPT, int C, int kmid, int kd,
                                  const HalfGeom& g, uint64_t key) {
-  if (TPT == 1) {
-#pragma unroll
-    for (int i = 0; i < P / 2; ++i) {
-      const u32x4 w = philox_call(alg2_call_index(2 * i, kmid, kd, g.Nmid, g.M), 0u, key);
-      v[2 * i] = box_muller(w.x, w.y, g.trig);
-      v[2 * i + 1] = box_muller(w.z, w.w, g.trig);
-    }
-  } else if (C < 32) {
-    const bool odd = (tau & 1) != 0;
-    // row k1 = tau + TPT qa has call ((k1 >> 1) Nmid + kmid)(M + 1) + kd; with TPT
-    // even, k1 >> 1 = (tau >> 1) + (TPT / 2) qa, so the calls step by a constant
-    const uint64_t stride = (uint64_t)(TPT >> 1) * (uint64_t)g.Nmid * (uint64_t)(g.M + 1);
-    uint64_t call = alg2_call_index(tau + (odd ? TPT * (P / 2) : 0), kmid, kd, g.Nmid, g.M);
-#pragma unroll
-    for (int i = 0; i < P / 2; ++i, call += stride) {  // this lane draws the call of its row qa
-      const u32x4 w = philox_call(call, 0u, key);
-      const uint32_t oa = odd ? w.z : w.x, ob = odd ? w.w : w.y;
-      const uint32_t pa = odd ? w.x : w.z, pb = odd ? w.y : w.w;
-      const uint32_t ra = __shfl_xor_sync(0xffffffffu, pa, C);
-      const uint32_t rb = __shfl_xor_sync(0xffffffffu, pb, C);
-      const float2 zo = box_muller(oa, ob, g.trig);  // own row qa
-      const float2 zr = box_muller(ra, rb, g.trig);  // own row qb, drawn by the partner
-      v[i] = odd ? zr : zo;
-      v[i + P / 2] = odd ? zo : zr;
-    }
+  if constexpr (NV == NV_INTHREAD) {
+    normals_inthread<P>(v, kmid, kd, g, key);
+  } else if constexpr (NV == NV_SHFL) {
+    normals_shfl<P>(v, tau, TPT, C, kmid, kd, g, key);
+  } else if constexpr (NV == NV_PLAIN) {
+    normals_plain<P>(v, tau, TPT, kmid, kd, g, key);
   } else {
-#pragma unroll
-    for (int q = 0; q < P; ++q) v[q] = alg2_normals_grid(tau + TPT * q, kmid, kd, g.Nmid, g.M, key, g.trig);
+    if (TPT == 1) normals_inthread<P>(v, kmid, kd, g, key);
+    else if (C < 32) normals_shfl<P>(v, tau, TPT, C, kmid, kd, g, key);
+    else normals_plain<P>(v, tau, TPT, kmid, kd, g, key);
   }
 }
 
@@ -132,7 +155,7 @@ GRF_DEV int64_t col_offset(const ColArgs& a, int pos, int col) {
 
 // Column `col` of the pass through its transforms: v[q] holds entry
 // pos = tau + TPT q.  `base` is the offset of the column's plane and field.
-template <int P, int SRC, int MODE>
+template <int P, int SRC, int MODE, int NV = NV_ANY>
 GRF_DEV void col_transform(const ColArgs& a, int col, bool valid, int64_t field, int64_t base, int tau, int c,
                            int C, int nthr, float2* sm, float2 (&v)[P], ColGeom& cg) {
   const int TPT = a.N / P;
@@ -144,7 +167,7 @@ GRF_DEV void col_transform(const ColArgs& a, int col, bool valid, int64_t field,
     const uint64_t key = g.seed + (uint64_t)(g.field0 + field);
     // s_K of this column: the folded table row (kd, fmid) is contiguous along axis 1
     const float* srow = g.stab + (cg.kd * (g.Nmid / 2 + 1) + min(cg.kmid, g.Nmid - cg.kmid)) * (g.N1 / 2 + 1);
-    alg2_column_normals<P>(v, tau, TPT, C, cg.kmid, cg.kd, g, key);
+    alg2_column_normals<P, NV>(v, tau, TPT, C, cg.kmid, cg.kd, g, key);
     // s_K read after the normals: the loads do not hold registers during the draw
     float s[P];
 #pragma unroll
@@ -241,7 +264,7 @@ GRF_DEV PairIdx pair_idx(const ColArgs& a, const Coords& co) {
   return r;
 }
 
-template <int P, int SRC, int MODE, class Coords>
+template <int P, int SRC, int MODE, int NV = NV_ANY, class Coords>
 GRF_DEV void col_body_pair(const ColArgs& a, const Coords& co, int nthr, float2* sm) {
   static_assert(MODE == COL_INV || MODE == COL_FWD_SCALE_INV, "pair mode ends an inverse pass");
   const int TPT = a.N / P;
@@ -249,7 +272,7 @@ GRF_DEV void col_body_pair(const ColArgs& a, const Coords& co, int nthr, float2*
   ColGeom cg;
   {
     const PairIdx x = pair_idx(a, co);
-    col_transform<P, SRC, MODE>(a, x.ca, x.valid, x.field, x.base, x.tau, x.c, a.C, nthr, sm, v, cg);
+    col_transform<P, SRC, MODE, NV>(a, x.ca, x.valid, x.field, x.base, x.tau, x.c, a.C, nthr, sm, v, cg);
   }
   float2* stash = sm + (size_t)spad(a.N) * a.C + co.tid();
 #pragma unroll
@@ -258,7 +281,7 @@ GRF_DEV void col_body_pair(const ColArgs& a, const Coords& co, int nthr, float2*
     // pair M/2 is one column: its second transform only keeps the CTA's
     // barriers in step (an in-place pass has already replaced its input)
     const PairIdx x = pair_idx(a, co);
-    col_transform<P, SRC, MODE>(a, x.cb, x.valid && x.ca != x.cb, x.field, x.base, x.tau, x.c, a.C, nthr, sm, v,
+    col_transform<P, SRC, MODE, NV>(a, x.cb, x.valid && x.ca != x.cb, x.field, x.base, x.tau, x.c, a.C, nthr, sm, v,
                                 cg);
   }
   const PairIdx x = pair_idx(a, co);
@@ -281,7 +304,7 @@ GRF_DEV void col_body_pair(const ColArgs& a, const Coords& co, int nthr, float2*
 
 // One CTA: C columns of plane `by` of field `bz`, X stored (or, for the
 // adjoint, reduced).
-template <int P, int SRC, int MODE>
+template <int P, int SRC, int MODE, int NV = NV_ANY>
 GRF_DEV void col_body(const ColArgs& a, int bx, int by, int64_t bz, int64_t blk, int nthr, float2* sm) {
   const int C = a.C;
   const int t = threadIdx.x;
@@ -295,7 +318,7 @@ GRF_DEV void col_body(const ColArgs& a, int bx, int by, int64_t bz, int64_t blk,
 
   const int col = bx * C + c;
   const bool valid = col < a.ncols;
-  col_transform<P, SRC, MODE>(a, col, valid, field, base, tau, c, C, nthr, sm, v, cg);
+  col_transform<P, SRC, MODE, NV>(a, col, valid, field, base, tau, c, C, nthr, sm, v, cg);
 
   if constexpr (MODE == COL_FWD_ADJ) {
     // v[q] = G^ at K = (k1, kmid, kd).  Sum w_K d_theta s_K Re(xi_K conj G^_K).

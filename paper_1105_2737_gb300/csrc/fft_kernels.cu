@@ -1,4 +1,6 @@
-// FP32 kernels of the sampling path, its Algorithm 1 mode and its adjoint.
+// Launchers of the FP32 passes of the sampling path, its Algorithm 1 mode and
+// its adjoint (the kernels are in pass_kernels.cuh; the noise pass, compiled
+// per noise variant, in noise_kernels.cu).
 //
 // Column pass (col_kernel): C consecutive columns of a plane, each a complex
 // sequence along a strided axis.  With COL_NOISE it is the first pass of
@@ -6,73 +8,19 @@
 // of its columns in registers (Philox4x32-10 + Box-Muller, the conjugate
 // rule of Eq. conj on the planes k_d in {0, N_d/2}), multiplies by s_K
 // (rule a) / Eq. drf) and runs the inverse FFT along axis 1; the noise never
-// touches memory.
+// touches memory.  The last column pass before the c2r pass runs in pair mode
+// and leaves Z of the c2r split (see col_body_pair).
 //
 // Row pass (row_kernel): C rows along the contiguous last axis.  ROW_C2R turns
-// the half spectrum (M+1 entries) into N = 2M reals with one M-point complex
-// inverse FFT: Z[k] = (X[k] + conj X[M-k]) + i e^{2 pi i k/N} (X[k] - conj X[M-k]),
+// Z[0..M-1] into N = 2M reals with one M-point complex inverse FFT,
 // z = IFFT_M(Z), f[2m] = Re z[m], f[2m+1] = Im z[m].  ROW_R2C is the forward
 // counterpart (pack x[2m] + i x[2m+1], FFT_M, split).
-#include "bodies.cuh"
+#include "pass_kernels.cuh"
 
 #include <mutex>
 
 namespace grf {
 
-
-template <int P, int SRC, int MODE, int PAIR>
-__global__ void __launch_bounds__(kMaxThreads<P>, kMinBlocks<P>) col_kernel(ColArgs a) {
-  extern __shared__ float2 sm[];
-  if constexpr (PAIR) {
-    col_body_pair<P, SRC, MODE>(a, CtaCoordsHW{}, blockDim.x, sm);
-  } else {
-    const int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    col_body<P, SRC, MODE>(a, blockIdx.x, blockIdx.y, blockIdx.z, blk, blockDim.x, sm);
-  }
-}
-
-template <int P, int SRC, int MODE>
-__global__ void __launch_bounds__(kMaxThreads<P>, kMinBlocks<P>) row_kernel(RowArgs a) {
-  extern __shared__ float2 sm[];
-  row_body<P, SRC, MODE>(a, blockIdx.x, blockDim.x, sm);
-}
-
-// Grid-stride forms of the two 2-D/3-D passes: `gridDim.x` CTAs walk all
-// tiles, so a small grid leaves room on every SM for another kernel's CTAs
-// (the pipelined schedule runs one CTA per SM of each pass side by side).
-template <int P, int SRC, int MODE, int PAIR>
-__global__ void __launch_bounds__(512) col_kernel_gs(ColArgs a, int gx, int gy, int gz) {
-  extern __shared__ float2 sm[];
-  const int64_t n = (int64_t)gx * gy * gz;
-  for (int64_t t = blockIdx.x; t < n; t += gridDim.x) {
-    const int bx = (int)(t % gx);
-    const int64_t r = t / gx;
-    if constexpr (PAIR) col_body_pair<P, SRC, MODE>(a, CtaCoordsVal{bx, (int)(r % gy), r / gy}, blockDim.x, sm);
-    else col_body<P, SRC, MODE>(a, bx, (int)(r % gy), r / gy, t, blockDim.x, sm);
-    __syncthreads();
-  }
-}
-
-template <int P, int SRC, int MODE>
-__global__ void __launch_bounds__(512) row_kernel_gs(RowArgs a, int64_t ntiles) {
-  extern __shared__ float2 sm[];
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    row_body<P, SRC, MODE>(a, t, blockDim.x, sm);
-    __syncthreads();
-  }
-}
-
-template <int P>
-__global__ void __launch_bounds__(512) fourstep_stage1(FourStepArgs a) {
-  extern __shared__ float2 sm[];
-  fourstep1_body<P>(a, blockIdx.x, blockIdx.z, blockDim.x, sm);
-}
-
-template <int P>
-__global__ void __launch_bounds__(512) fourstep_stage2(FourStepArgs a) {
-  extern __shared__ float2 sm[];
-  fourstep2_body<P>(a, blockIdx.x, blockIdx.z, blockDim.x, sm);
-}
 
 // ---------------------------------------------------------------------------
 // Launchers
@@ -137,36 +85,24 @@ cudaError_t prepare_kernel(const void* k, int threads, size_t smem) {
   return cudaSuccess;
 }
 
-template <int P, int SRC, int MODE, int PAIR>
-static cudaError_t launch_col_t(const ColArgs& a, dim3 grid, cudaStream_t s) {
-  const int threads = a.C * a.N / P;
-  const size_t smem = PAIR ? col_pair_smem_bytes(a.N, a.C) : col_smem_bytes(a.N, a.C);
-  auto k = col_kernel<P, SRC, MODE, PAIR>;
-  cudaError_t e = prepare_kernel((const void*)k, threads, smem);
-  if (e != cudaSuccess) return e;
-  k<<<grid, threads, smem, s>>>(a);
-  return cudaGetLastError();
-}
-
 template <int SRC, int MODE, int PAIR = 0>
 static cudaError_t launch_col_p(int P, const ColArgs& a, dim3 grid, cudaStream_t s) {
   switch (P) {
-    case 2: return launch_col_t<2, SRC, MODE, PAIR>(a, grid, s);
-    case 4: return launch_col_t<4, SRC, MODE, PAIR>(a, grid, s);
-    case 8: return launch_col_t<8, SRC, MODE, PAIR>(a, grid, s);
-    case 16: return launch_col_t<16, SRC, MODE, PAIR>(a, grid, s);
+    case 2: return launch_col_t<2, SRC, MODE, PAIR, NV_ANY>(a, grid, s);
+    case 4: return launch_col_t<4, SRC, MODE, PAIR, NV_ANY>(a, grid, s);
+    case 8: return launch_col_t<8, SRC, MODE, PAIR, NV_ANY>(a, grid, s);
+    case 16: return launch_col_t<16, SRC, MODE, PAIR, NV_ANY>(a, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_col(int src, int mode, int P, const ColArgs& a, dim3 grid, cudaStream_t s) {
+  if (src == COL_NOISE && mode == COL_INV) return launch_col_noise(P, a, grid, s);
   if (a.zpair) {  // the inverse passes that end before the c2r pass
-    if (src == COL_NOISE && mode == COL_INV) return launch_col_p<COL_NOISE, COL_INV, 1>(P, a, grid, s);
     if (src == COL_LOAD && mode == COL_INV) return launch_col_p<COL_LOAD, COL_INV, 1>(P, a, grid, s);
     if (src == COL_LOAD && mode == COL_FWD_SCALE_INV) return launch_col_p<COL_LOAD, COL_FWD_SCALE_INV, 1>(P, a, grid, s);
     return cudaErrorInvalidValue;
   }
-  if (src == COL_NOISE && mode == COL_INV) return launch_col_p<COL_NOISE, COL_INV>(P, a, grid, s);
   if (src == COL_LOAD && mode == COL_INV) return launch_col_p<COL_LOAD, COL_INV>(P, a, grid, s);
   if (src == COL_LOAD && mode == COL_FWD) return launch_col_p<COL_LOAD, COL_FWD>(P, a, grid, s);
   if (src == COL_LOAD && mode == COL_FWD_SCALE_INV) return launch_col_p<COL_LOAD, COL_FWD_SCALE_INV>(P, a, grid, s);
@@ -230,44 +166,24 @@ cudaError_t launch_fourstep(int stage, int P, const FourStepArgs& a, int64_t nfi
 }
 
 template <int P>
-static cudaError_t launch_gs_t(int which, const ColArgs* ca, const RowArgs* ra, dim3 tiles, int ctas,
-                               cudaStream_t s) {
-  if (which == 0) {
-    const int threads = ca->C * ca->N / P;
-    const size_t smem = ca->zpair ? col_pair_smem_bytes(ca->N, ca->C) : col_smem_bytes(ca->N, ca->C);
-    auto k = ca->zpair ? col_kernel_gs<P, COL_NOISE, COL_INV, 1> : col_kernel_gs<P, COL_NOISE, COL_INV, 0>;
-    cudaError_t e = prepare_kernel((const void*)k, threads, smem);
-    if (e != cudaSuccess) return e;
-    k<<<ctas, threads, smem, s>>>(*ca, tiles.x, tiles.y, tiles.z);
-  } else {
-    const int threads = ra->C * (ra->M / P);
-    const size_t smem = row_smem_bytes(ra->M, ra->C);
-    auto k = row_kernel_gs<P, ROW_LOAD_Z, ROW_C2R>;
-    cudaError_t e = prepare_kernel((const void*)k, threads, smem);
-    if (e != cudaSuccess) return e;
-    k<<<ctas, threads, smem, s>>>(*ra, (int64_t)tiles.x);
-  }
+static cudaError_t launch_row_gs_t(const RowArgs* ra, dim3 tiles, int ctas, cudaStream_t s) {
+  const int threads = ra->C * (ra->M / P);
+  const size_t smem = row_smem_bytes(ra->M, ra->C);
+  auto k = row_kernel_gs<P, ROW_LOAD_Z, ROW_C2R>;
+  cudaError_t e = prepare_kernel((const void*)k, threads, smem);
+  if (e != cudaSuccess) return e;
+  k<<<ctas, threads, smem, s>>>(*ra, (int64_t)tiles.x);
   return cudaGetLastError();
-}
-
-cudaError_t launch_col_noise_gs(int P, const ColArgs& a, dim3 tiles, int ctas, cudaStream_t s) {
-  switch (P) {
-    case 2: return launch_gs_t<2>(0, &a, nullptr, tiles, ctas, s);
-    case 4: return launch_gs_t<4>(0, &a, nullptr, tiles, ctas, s);
-    case 8: return launch_gs_t<8>(0, &a, nullptr, tiles, ctas, s);
-    case 16: return launch_gs_t<16>(0, &a, nullptr, tiles, ctas, s);
-    default: return cudaErrorInvalidValue;
-  }
 }
 
 cudaError_t launch_row_c2r_gs(int P, const RowArgs& a, int64_t ntiles, int ctas, cudaStream_t s) {
   const dim3 t((unsigned)ntiles);
   switch (P) {
-    case 1: return launch_gs_t<1>(1, nullptr, &a, t, ctas, s);
-    case 2: return launch_gs_t<2>(1, nullptr, &a, t, ctas, s);
-    case 4: return launch_gs_t<4>(1, nullptr, &a, t, ctas, s);
-    case 8: return launch_gs_t<8>(1, nullptr, &a, t, ctas, s);
-    case 16: return launch_gs_t<16>(1, nullptr, &a, t, ctas, s);
+    case 1: return launch_row_gs_t<1>(&a, t, ctas, s);
+    case 2: return launch_row_gs_t<2>(&a, t, ctas, s);
+    case 4: return launch_row_gs_t<4>(&a, t, ctas, s);
+    case 8: return launch_row_gs_t<8>(&a, t, ctas, s);
+    case 16: return launch_row_gs_t<16>(&a, t, ctas, s);
     default: return cudaErrorInvalidValue;
   }
 }

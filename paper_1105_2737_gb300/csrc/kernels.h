@@ -14,6 +14,10 @@ enum ColMode {
   COL_FWD_ADJ = 3         // forward, then reduce against regenerated xi (adjoint)
 };
 
+// How the noise pass deals Philox words to threads (see alg2_column_normals).
+enum NoiseVariant { NV_SHFL = 0, NV_INTHREAD = 1, NV_PLAIN = 2, NV_ANY = 3 };
+inline int noise_variant(int N, int P, int C) { return N == P ? NV_INTHREAD : (C < 32 ? NV_SHFL : NV_PLAIN); }
+
 // Sources and modes of the row pass (the contiguous last axis).
 //   ROW_LOAD_Z: Z[k] = (X[k] + conj X[M-k]) + i e^{2 pi i k/N} (X[k] - conj X[M-k]),
 //   k < M, as the last column pass leaves it (pair mode) in the half-spectrum
@@ -107,6 +111,8 @@ cudaError_t launch_fourstep(int stage, int P, const FourStepArgs& a, int64_t nfi
 // transform (16 if the length is >= 16, else the length itself).
 cudaError_t launch_col(int src, int mode, int P, const ColArgs& a, dim3 grid, cudaStream_t s);
 cudaError_t launch_row(int src, int mode, int P, const RowArgs& a, dim3 grid, cudaStream_t s);
+// The noise + axis-1 pass (noise_kernels.cu), compiled per noise variant.
+cudaError_t launch_col_noise(int P, const ColArgs& a, dim3 grid, cudaStream_t s);
 // Grid-stride forms (ctas CTAs walk all tiles) of the noise + axis-1 pass and the c2r pass.
 cudaError_t launch_col_noise_gs(int P, const ColArgs& a, dim3 tiles, int ctas, cudaStream_t s);
 cudaError_t launch_row_c2r_gs(int P, const RowArgs& a, int64_t ntiles, int ctas, cudaStream_t s);

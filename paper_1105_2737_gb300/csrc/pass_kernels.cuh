@@ -1,0 +1,74 @@
+// The __global__ kernels of the FP32 passes (templates), shared by the
+// translation units that instantiate them (fft_kernels.cu, noise_kernels.cu),
+// and the launch helper of the column kernels.
+#pragma once
+#include "bodies.cuh"
+
+namespace grf {
+
+template <int P, int SRC, int MODE, int PAIR, int NV>
+__global__ void __launch_bounds__(kMaxThreads<P>, kMinBlocks<P>) col_kernel(ColArgs a) {
+  extern __shared__ float2 sm[];
+  if constexpr (PAIR) {
+    col_body_pair<P, SRC, MODE, NV>(a, CtaCoordsHW{}, blockDim.x, sm);
+  } else {
+    const int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    col_body<P, SRC, MODE, NV>(a, blockIdx.x, blockIdx.y, blockIdx.z, blk, blockDim.x, sm);
+  }
+}
+
+template <int P, int SRC, int MODE>
+__global__ void __launch_bounds__(kMaxThreads<P>, kMinBlocks<P>) row_kernel(RowArgs a) {
+  extern __shared__ float2 sm[];
+  row_body<P, SRC, MODE>(a, blockIdx.x, blockDim.x, sm);
+}
+
+// Grid-stride forms of the two 2-D/3-D passes: `gridDim.x` CTAs walk all
+// tiles, so a small grid leaves room on every SM for another kernel's CTAs
+// (the pipelined schedule runs one CTA per SM of each pass side by side).
+template <int P, int SRC, int MODE, int PAIR>
+__global__ void __launch_bounds__(512) col_kernel_gs(ColArgs a, int gx, int gy, int gz) {
+  extern __shared__ float2 sm[];
+  const int64_t n = (int64_t)gx * gy * gz;
+  for (int64_t t = blockIdx.x; t < n; t += gridDim.x) {
+    const int bx = (int)(t % gx);
+    const int64_t r = t / gx;
+    if constexpr (PAIR) col_body_pair<P, SRC, MODE>(a, CtaCoordsVal{bx, (int)(r % gy), r / gy}, blockDim.x, sm);
+    else col_body<P, SRC, MODE>(a, bx, (int)(r % gy), r / gy, t, blockDim.x, sm);
+    __syncthreads();
+  }
+}
+
+template <int P, int SRC, int MODE>
+__global__ void __launch_bounds__(512) row_kernel_gs(RowArgs a, int64_t ntiles) {
+  extern __shared__ float2 sm[];
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    row_body<P, SRC, MODE>(a, t, blockDim.x, sm);
+    __syncthreads();
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(512) fourstep_stage1(FourStepArgs a) {
+  extern __shared__ float2 sm[];
+  fourstep1_body<P>(a, blockIdx.x, blockIdx.z, blockDim.x, sm);
+}
+
+template <int P>
+__global__ void __launch_bounds__(512) fourstep_stage2(FourStepArgs a) {
+  extern __shared__ float2 sm[];
+  fourstep2_body<P>(a, blockIdx.x, blockIdx.z, blockDim.x, sm);
+}
+
+template <int P, int SRC, int MODE, int PAIR, int NV>
+static cudaError_t launch_col_t(const ColArgs& a, dim3 grid, cudaStream_t s) {
+  const int threads = a.C * a.N / P;
+  const size_t smem = PAIR ? col_pair_smem_bytes(a.N, a.C) : col_smem_bytes(a.N, a.C);
+  auto k = col_kernel<P, SRC, MODE, PAIR, NV>;
+  cudaError_t e = prepare_kernel((const void*)k, threads, smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, threads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace grf
