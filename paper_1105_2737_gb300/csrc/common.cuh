@@ -77,7 +77,12 @@ GRF_DEV double uniform_open_d(uint32_t x) {
 }
 
 // Box-Muller: rho = sqrt(-2 ln u_a), (z_re, z_im) = rho (cos 2 pi u_b, sin 2 pi u_b).
-// CUDA's accurate logf is called.  The angle: u_b = m' 2^-24 with m' = 2 (x >> 9) + 1
+// ln u_a: CUDA's fast __logf, whose error is at most 3 ulp for u < 0.5 and at
+// most 2^-21.41 absolute on [0.5, 2); within 2^-7 of 1, where that bound would
+// be large against |ln u|, the series ln(1 - t) = -(t + t^2/2 + t^3/3 + t^4/4)
+// (truncation below 2^-28 relative) on t = 1 - u, which is exact (Sterbenz).
+// Both are formed and one is selected, without a branch.
+// The angle: u_b = m' 2^-24 with m' = 2 (x >> 9) + 1
 // an odd 24-bit integer, so 2 pi u_b = a + delta exactly, with the coarse angle
 // a = 2 pi (m' >> 16) / 256 and delta = 2 pi (m' & 0xFFFF) 2^-24 in [0, 0.0246).
 // cos a, sin a come from `trig` (trig[h] = exp(2 pi i h / 256), built in FP64);
@@ -85,7 +90,9 @@ GRF_DEV double uniform_open_d(uint32_t x) {
 // angle-addition formulas combine them.  Error: a few FP32 ulps.
 GRF_DEV float2 box_muller(uint32_t wa, uint32_t wb, const float2* __restrict__ trig) {
   const float ua = uniform_open(wa);
-  const float rho2 = -2.0f * logf(ua);
+  const float ta = 1.0f - ua;
+  const float near1 = -ta * fmaf(ta, fmaf(ta, fmaf(ta, 0.25f, 0.333333343f), 0.5f), 1.0f);
+  const float rho2 = -2.0f * (ta < 0.0078125f ? near1 : __logf(ua));
   const float rho = rho2 * rsqrtf(rho2);
   // m' >> 16 = wb >> 24; m' & 0xFFFF = 2 r + 1 with r = (wb >> 9) & 0x7FFF, and
   // (2 r + 1) 2^-16 is formed exactly from the bits as in uniform_open, then
