@@ -257,6 +257,9 @@ def _sampled_rows(n, Lb, spec, seed, fields, rows):
 @pytest.mark.parametrize("shape,fam,kw,batch,fields,rows", [
     ((4096, 4096), "matern", dict(ell=0.05, nu=2.5), 64, [0, 37, 63], [(0,), (1,), (2047,), (2048,), (4095,)]),
     ((4096, 4096), "matern", dict(ell=0.01, nu=0.5), 64, [5], [(0,), (3000,)]),
+    # rough and short-range: s_K decays slowly, so an error with a nonzero mean
+    # over the modes adds up coherently at points like (0, 0)
+    ((4096, 4096), "matern", dict(ell=0.002, nu=0.5), 64, [3], [(0,), (777,)]),
     ((512, 512), "matern", dict(ell=0.05, nu=0.5), 64, [0, 63], [(0,), (255,), (511,)]),
     ((256, 256, 256), "gaussian", dict(ell=0.03), 8, [0, 7], [(0, 0), (128, 5), (255, 255)]),
 ])
