@@ -155,10 +155,14 @@ GRF_DEV int64_t col_offset(const ColArgs& a, int pos, int col) {
 
 // Column `col` of the pass through its transforms: v[q] holds entry
 // pos = tau + TPT q.  `base` is the offset of the column's plane and field.
-template <int P, int SRC, int MODE, int NV = NV_ANY>
+// LN, CC: a compile-time transform length 2^LN and CC columns per CTA (see
+// pass_kernels.cuh); 0 takes them from the launch descriptor.
+template <int P, int SRC, int MODE, int NV = NV_ANY, int LN = 0>
 GRF_DEV void col_transform(const ColArgs& a, int col, bool valid, int64_t field, int64_t base, int tau, int c,
                            int C, int nthr, float2* sm, float2 (&v)[P], ColGeom& cg) {
-  const int TPT = a.N / P;
+  const int N = LN ? (1 << LN) : a.N;
+  const int logN = LN ? LN : a.logN;
+  const int TPT = N / P;
   cg = ColGeom{0, 0};
   if (SRC == COL_NOISE || MODE == COL_FWD_SCALE_INV || MODE == COL_FWD_ADJ) cg = col_geom(valid ? col : 0, a.g);
 
@@ -197,9 +201,9 @@ GRF_DEV void col_transform(const ColArgs& a, int col, bool valid, int64_t field,
   }
 
   if constexpr (MODE == COL_INV) {
-    fft_core<P, +1>(v, sm, tau, c, C, a.N, a.logN, a.tw, a.tws, nthr);
+    fft_core<P, +1>(v, sm, tau, c, C, N, logN, a.tw, a.tws, nthr);
   } else {
-    fft_core<P, -1>(v, sm, tau, c, C, a.N, a.logN, a.tw, a.tws, nthr);
+    fft_core<P, -1>(v, sm, tau, c, C, N, logN, a.tw, a.tws, nthr);
   }
 
   if constexpr (MODE == COL_FWD_SCALE_INV) {
@@ -209,7 +213,7 @@ GRF_DEV void col_transform(const ColArgs& a, int col, bool valid, int64_t field,
       const float s = valid ? __ldg(a.g.stab + fold_index(k1, cg.kmid, cg.kd, a.g)) * a.g.alg1_scale : 0.f;
       v[q] = cscale(v[q], s);
     }
-    fft_core<P, +1>(v, sm, tau, c, C, a.N, a.logN, a.tw, a.tws, nthr);
+    fft_core<P, +1>(v, sm, tau, c, C, N, logN, a.tw, a.tws, nthr);
   }
 }
 
@@ -249,13 +253,14 @@ struct PairIdx {
   bool valid;
   int64_t field, base;
 };
-template <class Coords>
+template <int CC, class Coords>
 GRF_DEV PairIdx pair_idx(const ColArgs& a, const Coords& co) {
   PairIdx r;
+  const int C = CC ? CC : a.C;
   const int t = co.tid();
-  r.c = t & (a.C - 1);
-  r.tau = t / a.C;
-  r.p = co.bx() * a.C + r.c;
+  r.c = t & (C - 1);
+  r.tau = t / C;
+  r.p = co.bx() * C + r.c;
   r.valid = r.p <= a.g.M / 2;
   r.ca = r.valid ? r.p : 0;
   r.cb = r.valid ? a.g.M - r.p : 0;
@@ -264,31 +269,34 @@ GRF_DEV PairIdx pair_idx(const ColArgs& a, const Coords& co) {
   return r;
 }
 
-template <int P, int SRC, int MODE, int NV = NV_ANY, class Coords>
-GRF_DEV void col_body_pair(const ColArgs& a, const Coords& co, int nthr, float2* sm) {
+template <int P, int SRC, int MODE, int NV = NV_ANY, int LN = 0, int CC = 0, class Coords>
+GRF_DEV void col_body_pair(const ColArgs& a, const Coords& co, int nthr_rt, float2* sm) {
   static_assert(MODE == COL_INV || MODE == COL_FWD_SCALE_INV, "pair mode ends an inverse pass");
-  const int TPT = a.N / P;
+  const int N = LN ? (1 << LN) : a.N;
+  const int C = CC ? CC : a.C;
+  const int nthr = (LN && CC) ? CC * (1 << LN) / P : nthr_rt;
+  const int TPT = N / P;
   float2 v[P];
   ColGeom cg;
   {
-    const PairIdx x = pair_idx(a, co);
-    col_transform<P, SRC, MODE, NV>(a, x.ca, x.valid, x.field, x.base, x.tau, x.c, a.C, nthr, sm, v, cg);
+    const PairIdx x = pair_idx<CC>(a, co);
+    col_transform<P, SRC, MODE, NV, LN>(a, x.ca, x.valid, x.field, x.base, x.tau, x.c, C, nthr, sm, v, cg);
   }
-  float2* stash = sm + (size_t)spad(a.N) * a.C + co.tid();
+  float2* stash = sm + (size_t)spad(N) * C + co.tid();
 #pragma unroll
   for (int q = 0; q < P; ++q) stash[q * nthr] = v[q];
   {
     // pair M/2 is one column: its second transform only keeps the CTA's
     // barriers in step (an in-place pass has already replaced its input)
-    const PairIdx x = pair_idx(a, co);
-    col_transform<P, SRC, MODE, NV>(a, x.cb, x.valid && x.ca != x.cb, x.field, x.base, x.tau, x.c, a.C, nthr, sm, v,
-                                cg);
+    const PairIdx x = pair_idx<CC>(a, co);
+    col_transform<P, SRC, MODE, NV, LN>(a, x.cb, x.valid && x.ca != x.cb, x.field, x.base, x.tau, x.c, C, nthr, sm,
+                                        v, cg);
   }
-  const PairIdx x = pair_idx(a, co);
+  const PairIdx x = pair_idx<CC>(a, co);
   if (!x.valid) return;
   float2* out = a.out + x.base;
   const float2 w = __ldg(a.twz + x.p);
-  stash = sm + (size_t)spad(a.N) * a.C + co.tid();
+  stash = sm + (size_t)spad(N) * C + co.tid();
 #pragma unroll
   for (int q = 0; q < P; ++q) {
     const int64_t oa = col_offset(a, x.tau + TPT * q, x.ca);
@@ -304,13 +312,14 @@ GRF_DEV void col_body_pair(const ColArgs& a, const Coords& co, int nthr, float2*
 
 // One CTA: C columns of plane `by` of field `bz`, X stored (or, for the
 // adjoint, reduced).
-template <int P, int SRC, int MODE, int NV = NV_ANY>
-GRF_DEV void col_body(const ColArgs& a, int bx, int by, int64_t bz, int64_t blk, int nthr, float2* sm) {
-  const int C = a.C;
+template <int P, int SRC, int MODE, int NV = NV_ANY, int LN = 0, int CC = 0>
+GRF_DEV void col_body(const ColArgs& a, int bx, int by, int64_t bz, int64_t blk, int nthr_rt, float2* sm) {
+  const int C = CC ? CC : a.C;
+  const int nthr = (LN && CC) ? CC * (1 << LN) / P : nthr_rt;
   const int t = threadIdx.x;
   const int c = t & (C - 1);
   const int tau = t / C;
-  const int TPT = a.N / P;
+  const int TPT = (LN ? (1 << LN) : a.N) / P;
   const int64_t field = bz;
   const int64_t base = field * a.bstride + (int64_t)by * a.ostride;
   float2 v[P];
@@ -318,7 +327,7 @@ GRF_DEV void col_body(const ColArgs& a, int bx, int by, int64_t bz, int64_t blk,
 
   const int col = bx * C + c;
   const bool valid = col < a.ncols;
-  col_transform<P, SRC, MODE, NV>(a, col, valid, field, base, tau, c, C, nthr, sm, v, cg);
+  col_transform<P, SRC, MODE, NV, LN>(a, col, valid, field, base, tau, c, C, nthr, sm, v, cg);
 
   if constexpr (MODE == COL_FWD_ADJ) {
     // v[q] = G^ at K = (k1, kmid, kd).  Sum w_K d_theta s_K Re(xi_K conj G^_K).
@@ -376,13 +385,17 @@ GRF_DEV float2 r2c_post(float2 Zk, float2 Zmk, float2 w) {
   return make_float2(0.5f * (A.x + wB.y), 0.5f * (A.y - wB.x));
 }
 
-template <int P, int SRC, int MODE>
-GRF_DEV void row_body(const RowArgs& a, int64_t bx, int nthr, float2* sm) {
-  const int C = a.C;
+// LN, CC: a compile-time length M = 2^LN and CC rows per CTA (see
+// pass_kernels.cuh); 0 takes them from the launch descriptor.
+template <int P, int SRC, int MODE, int LN = 0, int CC = 0>
+GRF_DEV void row_body(const RowArgs& a, int64_t bx, int nthr_rt, float2* sm) {
+  const int C = CC ? CC : a.C;
+  const int nthr = (LN && CC) ? CC * (1 << LN) / P : nthr_rt;
   const int t = threadIdx.x;
   const int c = t & (C - 1);
   const int tau = t / C;
-  const int M = a.M;
+  const int M = LN ? (1 << LN) : a.M;
+  const int logM = LN ? LN : a.logM;
   const int N = 2 * M;
   const int TPT = M / P;
   const int64_t g = bx * C + c;
@@ -398,7 +411,7 @@ GRF_DEV void row_body(const RowArgs& a, int64_t bx, int nthr, float2* sm) {
 #pragma unroll
     for (int q = 0; q < P; ++q)
       v[q] = valid ? __ldcg(src + ((int64_t)(tau + TPT * q) << a.logT)) : make_float2(0.f, 0.f);
-    fft_core<P, +1>(v, sm, tau, c, C, M, a.logM, a.twM, a.tws, nthr);
+    fft_core<P, +1>(v, sm, tau, c, C, M, logM, a.twM, a.tws, nthr);
     if (valid) {
       float2* o = reinterpret_cast<float2*>(a.outR + g * N);
 #pragma unroll
@@ -431,7 +444,7 @@ GRF_DEV void row_body(const RowArgs& a, int64_t bx, int nthr, float2* sm) {
       v[q] = c2r_pre(sm[spad(k) * C + c], sm[spad(M - k) * C + c], __ldg(a.twN + k));
     }
     if constexpr (P < 16) cta_sync(nthr);
-    fft_core<P, +1>(v, sm, tau, c, C, M, a.logM, a.twM, a.tws, nthr);
+    fft_core<P, +1>(v, sm, tau, c, C, M, logM, a.twM, a.tws, nthr);
     if (valid) {
       float2* o = reinterpret_cast<float2*>(a.outR + g * N);
 #pragma unroll
@@ -454,7 +467,7 @@ GRF_DEV void row_body(const RowArgs& a, int64_t bx, int nthr, float2* sm) {
       }
       v[q] = z;
     }
-    fft_core<P, -1>(v, sm, tau, c, C, M, a.logM, a.twM, a.tws, nthr);
+    fft_core<P, -1>(v, sm, tau, c, C, M, logM, a.twM, a.tws, nthr);
     cta_sync(nthr);
 #pragma unroll
     for (int q = 0; q < P; ++q) sm[spad(tau + TPT * q) * C + c] = v[q];
@@ -494,7 +507,7 @@ GRF_DEV void row_body(const RowArgs& a, int64_t bx, int nthr, float2* sm) {
         v[q] = c2r_pre(X[q], sm[spad(M - k) * C + c], __ldg(a.twN + k));
       }
       if constexpr (P < 16) cta_sync(nthr);
-      fft_core<P, +1>(v, sm, tau, c, C, M, a.logM, a.twM, a.tws, nthr);
+      fft_core<P, +1>(v, sm, tau, c, C, M, logM, a.twM, a.tws, nthr);
       if (valid) {
         float2* o = reinterpret_cast<float2*>(a.outR + g * N);
 #pragma unroll

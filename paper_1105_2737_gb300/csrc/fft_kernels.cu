@@ -98,6 +98,8 @@ static cudaError_t launch_col_p(int P, const ColArgs& a, dim3 grid, cudaStream_t
 
 cudaError_t launch_col(int src, int mode, int P, const ColArgs& a, dim3 grid, cudaStream_t s) {
   if (src == COL_NOISE && mode == COL_INV) return launch_col_noise(P, a, grid, s);
+  cudaError_t e;
+  if (src == COL_LOAD && mode == COL_INV && a.zpair && launch_col_load_pair_spec(P, a, grid, s, &e)) return e;
   if (a.zpair) {  // the inverse passes that end before the c2r pass
     if (src == COL_LOAD && mode == COL_INV) return launch_col_p<COL_LOAD, COL_INV, 1>(P, a, grid, s);
     if (src == COL_LOAD && mode == COL_FWD_SCALE_INV) return launch_col_p<COL_LOAD, COL_FWD_SCALE_INV, 1>(P, a, grid, s);
@@ -108,21 +110,6 @@ cudaError_t launch_col(int src, int mode, int P, const ColArgs& a, dim3 grid, cu
   if (src == COL_LOAD && mode == COL_FWD_SCALE_INV) return launch_col_p<COL_LOAD, COL_FWD_SCALE_INV>(P, a, grid, s);
   if (src == COL_LOAD && mode == COL_FWD_ADJ) return launch_col_p<COL_LOAD, COL_FWD_ADJ>(P, a, grid, s);
   return cudaErrorInvalidValue;
-}
-
-template <int P, int SRC, int MODE>
-static cudaError_t launch_row_t(const RowArgs& a, dim3 grid, cudaStream_t s) {
-  const int threads = a.C * (a.M / P);
-  size_t smem = row_smem_bytes(a.M, a.C);
-  if (MODE == ROW_R2C_ADJ) {
-    const size_t need = (size_t)threads * 3 * sizeof(double);
-    if (need > smem) smem = need;
-  }
-  auto k = row_kernel<P, SRC, MODE>;
-  cudaError_t e = prepare_kernel((const void*)k, threads, smem);
-  if (e != cudaSuccess) return e;
-  k<<<grid, threads, smem, s>>>(a);
-  return cudaGetLastError();
 }
 
 template <int SRC, int MODE>
@@ -189,7 +176,11 @@ cudaError_t launch_row_c2r_gs(int P, const RowArgs& a, int64_t ntiles, int ctas,
 }
 
 cudaError_t launch_row(int src, int mode, int P, const RowArgs& a, dim3 grid, cudaStream_t s) {
-  if (src == ROW_LOAD_Z && mode == ROW_C2R) return launch_row_p<ROW_LOAD_Z, ROW_C2R>(P, a, grid, s);
+  if (src == ROW_LOAD_Z && mode == ROW_C2R) {
+    cudaError_t e;
+    if (launch_row_c2r_spec(P, a, grid, s, &e)) return e;
+    return launch_row_p<ROW_LOAD_Z, ROW_C2R>(P, a, grid, s);
+  }
   if (src == ROW_NOISE_H && mode == ROW_C2R) return launch_row_p<ROW_NOISE_H, ROW_C2R>(P, a, grid, s);
   if (src == ROW_LOAD_REAL && mode == ROW_R2C) return launch_row_p<ROW_LOAD_REAL, ROW_R2C>(P, a, grid, s);
   if (src == ROW_NOISE_REAL && mode == ROW_R2C) return launch_row_p<ROW_NOISE_REAL, ROW_R2C>(P, a, grid, s);

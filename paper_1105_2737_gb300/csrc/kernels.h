@@ -113,6 +113,11 @@ cudaError_t launch_col(int src, int mode, int P, const ColArgs& a, dim3 grid, cu
 cudaError_t launch_row(int src, int mode, int P, const RowArgs& a, dim3 grid, cudaStream_t s);
 // The noise + axis-1 pass (noise_kernels.cu), compiled per noise variant.
 cudaError_t launch_col_noise(int P, const ColArgs& a, dim3 grid, cudaStream_t s);
+// Compile-time-geometry forms (spec_*.cu): launch and return true if the
+// launch has one, else return false and launch nothing.
+bool launch_col_noise_spec(int P, const ColArgs& a, dim3 grid, cudaStream_t s, cudaError_t* err);
+bool launch_col_load_pair_spec(int P, const ColArgs& a, dim3 grid, cudaStream_t s, cudaError_t* err);
+bool launch_row_c2r_spec(int P, const RowArgs& a, dim3 grid, cudaStream_t s, cudaError_t* err);
 // Grid-stride forms (ctas CTAs walk all tiles) of the noise + axis-1 pass and the c2r pass.
 cudaError_t launch_col_noise_gs(int P, const ColArgs& a, dim3 tiles, int ctas, cudaStream_t s);
 cudaError_t launch_row_c2r_gs(int P, const RowArgs& a, int64_t ntiles, int ctas, cudaStream_t s);

@@ -48,6 +48,8 @@ cudaError_t launch_noise_gs_t(const ColArgs& a, dim3 tiles, int ctas, cudaStream
 }  // namespace
 
 cudaError_t launch_col_noise(int P, const ColArgs& a, dim3 grid, cudaStream_t s) {
+  cudaError_t e;
+  if (launch_col_noise_spec(P, a, grid, s, &e)) return e;
   return a.zpair ? launch_noise_p<1>(P, a, grid, s) : launch_noise_p<0>(P, a, grid, s);
 }
 

@@ -6,21 +6,35 @@
 
 namespace grf {
 
-template <int P, int SRC, int MODE, int PAIR, int NV>
+// LN, CC != 0: the transform length 2^LN and the columns (rows) per CTA are
+// compile-time constants, so the stage loop unrolls and every shared-memory
+// and twiddle address of the exchanges is a constant offset.  These forms are
+// compiled for the 256-thread radix-16 geometries (C N = 4096) and chosen by
+// the launchers; LN = CC = 0 is the general kernel.
+template <int P, int SRC, int MODE, int PAIR, int NV, int LN = 0, int CC = 0>
 __global__ void __launch_bounds__(kMaxThreads<P>, kMinBlocks<P>) col_kernel(ColArgs a) {
   extern __shared__ float2 sm[];
   if constexpr (PAIR) {
-    col_body_pair<P, SRC, MODE, NV>(a, CtaCoordsHW{}, blockDim.x, sm);
+    col_body_pair<P, SRC, MODE, NV, LN, CC>(a, CtaCoordsHW{}, blockDim.x, sm);
   } else {
     const int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    col_body<P, SRC, MODE, NV>(a, blockIdx.x, blockIdx.y, blockIdx.z, blk, blockDim.x, sm);
+    col_body<P, SRC, MODE, NV, LN, CC>(a, blockIdx.x, blockIdx.y, blockIdx.z, blk, blockDim.x, sm);
   }
 }
 
-template <int P, int SRC, int MODE>
+template <int P, int SRC, int MODE, int LN = 0, int CC = 0>
 __global__ void __launch_bounds__(kMaxThreads<P>, kMinBlocks<P>) row_kernel(RowArgs a) {
   extern __shared__ float2 sm[];
-  row_body<P, SRC, MODE>(a, blockIdx.x, blockDim.x, sm);
+  row_body<P, SRC, MODE, LN, CC>(a, blockIdx.x, blockDim.x, sm);
+}
+
+// log2 N if (N, C) is one of the compile-time radix-16 geometries (C N = 4096,
+// 256 threads, N in [lo, hi]), else 0.
+inline int spec_ln(int P, int N, int C, int lo, int hi) {
+  if (P != 16 || N < lo || N > hi || (N & (N - 1)) || (int64_t)C * N != 4096) return 0;
+  int l = 0;
+  while ((1 << l) < N) ++l;
+  return l;
 }
 
 // Grid-stride forms of the two 2-D/3-D passes: `gridDim.x` CTAs walk all
@@ -60,11 +74,26 @@ __global__ void __launch_bounds__(512) fourstep_stage2(FourStepArgs a) {
   fourstep2_body<P>(a, blockIdx.x, blockIdx.z, blockDim.x, sm);
 }
 
-template <int P, int SRC, int MODE, int PAIR, int NV>
+template <int P, int SRC, int MODE, int PAIR, int NV, int LN = 0, int CC = 0>
 static cudaError_t launch_col_t(const ColArgs& a, dim3 grid, cudaStream_t s) {
   const int threads = a.C * a.N / P;
   const size_t smem = PAIR ? col_pair_smem_bytes(a.N, a.C) : col_smem_bytes(a.N, a.C);
-  auto k = col_kernel<P, SRC, MODE, PAIR, NV>;
+  auto k = col_kernel<P, SRC, MODE, PAIR, NV, LN, CC>;
+  cudaError_t e = prepare_kernel((const void*)k, threads, smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, threads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int P, int SRC, int MODE, int LN = 0, int CC = 0>
+static cudaError_t launch_row_t(const RowArgs& a, dim3 grid, cudaStream_t s) {
+  const int threads = a.C * (a.M / P);
+  size_t smem = row_smem_bytes(a.M, a.C);
+  if (MODE == ROW_R2C_ADJ) {
+    const size_t need = (size_t)threads * 3 * sizeof(double);
+    if (need > smem) smem = need;
+  }
+  auto k = row_kernel<P, SRC, MODE, LN, CC>;
   cudaError_t e = prepare_kernel((const void*)k, threads, smem);
   if (e != cudaSuccess) return e;
   k<<<grid, threads, smem, s>>>(a);

@@ -1,0 +1,43 @@
+// The axis-2 pair pass (3-D) and the c2r pass compiled for fixed radix-16
+// geometries: length 2^LN with 4096 / 2^LN columns or rows per CTA, 256
+// threads (see pass_kernels.cuh).
+#include "pass_kernels.cuh"
+
+namespace grf {
+
+namespace {
+
+template <int LN>
+cudaError_t load_pair_t(const ColArgs& a, dim3 grid, cudaStream_t s) {
+  return launch_col_t<16, COL_LOAD, COL_INV, 1, NV_ANY, LN, (4096 >> LN)>(a, grid, s);
+}
+template <int LN>
+cudaError_t row_c2r_t(const RowArgs& a, dim3 grid, cudaStream_t s) {
+  return launch_row_t<16, ROW_LOAD_Z, ROW_C2R, LN, (4096 >> LN)>(a, grid, s);
+}
+
+}  // namespace
+
+bool launch_col_load_pair_spec(int P, const ColArgs& a, dim3 grid, cudaStream_t s, cudaError_t* err) {
+  switch (spec_ln(P, a.N, a.C, 256, 4096)) {
+    case 8: *err = load_pair_t<8>(a, grid, s); return true;
+    case 9: *err = load_pair_t<9>(a, grid, s); return true;
+    case 10: *err = load_pair_t<10>(a, grid, s); return true;
+    case 11: *err = load_pair_t<11>(a, grid, s); return true;
+    case 12: *err = load_pair_t<12>(a, grid, s); return true;
+    default: return false;
+  }
+}
+
+bool launch_row_c2r_spec(int P, const RowArgs& a, dim3 grid, cudaStream_t s, cudaError_t* err) {
+  switch (spec_ln(P, a.M, a.C, 128, 2048)) {
+    case 7: *err = row_c2r_t<7>(a, grid, s); return true;
+    case 8: *err = row_c2r_t<8>(a, grid, s); return true;
+    case 9: *err = row_c2r_t<9>(a, grid, s); return true;
+    case 10: *err = row_c2r_t<10>(a, grid, s); return true;
+    case 11: *err = row_c2r_t<11>(a, grid, s); return true;
+    default: return false;
+  }
+}
+
+}  // namespace grf
