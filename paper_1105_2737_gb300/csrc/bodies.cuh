@@ -278,25 +278,49 @@ GRF_DEV void col_body_pair(const ColArgs& a, const Coords& co, int nthr_rt, floa
   const int TPT = N / P;
   float2 v[P];
   ColGeom cg;
-  {
-    const PairIdx x = pair_idx<CC>(a, co);
-    col_transform<P, SRC, MODE, NV, LN>(a, x.ca, x.valid, x.field, x.base, x.tau, x.c, C, nthr, sm, v, cg);
-  }
-  float2* stash = sm + (size_t)spad(N) * C + co.tid();
+  if constexpr (SRC == COL_LOAD && MODE == COL_INV && P <= 8) {
+    // loaded pair (3-D axis 2): both columns are read before either is
+    // transformed (2 P complex values fit in the registers at P <= 8), so the
+    // second column's loads overlap the first transform
+    const int logN = LN ? LN : a.logN;
+    float2 vb[P];
+    {
+      const PairIdx x = pair_idx<CC>(a, co);
 #pragma unroll
-  for (int q = 0; q < P; ++q) stash[q * nthr] = v[q];
-  {
-    // pair M/2 is one column: its second transform only keeps the CTA's
-    // barriers in step (an in-place pass has already replaced its input)
-    const PairIdx x = pair_idx<CC>(a, co);
-    col_transform<P, SRC, MODE, NV, LN>(a, x.cb, x.valid && x.ca != x.cb, x.field, x.base, x.tau, x.c, C, nthr, sm,
-                                        v, cg);
+      for (int q = 0; q < P; ++q) {
+        const int pos = x.tau + TPT * q;
+        v[q] = x.valid ? __ldcg(a.in + x.base + col_offset(a, pos, x.ca)) : make_float2(0.f, 0.f);
+        vb[q] = x.valid ? __ldcg(a.in + x.base + col_offset(a, pos, x.cb)) : make_float2(0.f, 0.f);
+      }
+    }
+    fft_core<P, +1>(v, sm, co.tid() / C, co.tid() & (C - 1), C, N, logN, a.tw, a.tws, nthr);
+    float2* stash = sm + (size_t)spad(N) * C + co.tid();
+#pragma unroll
+    for (int q = 0; q < P; ++q) stash[q * nthr] = v[q];
+#pragma unroll
+    for (int q = 0; q < P; ++q) v[q] = vb[q];
+    fft_core<P, +1>(v, sm, co.tid() / C, co.tid() & (C - 1), C, N, logN, a.tw, a.tws, nthr);
+  } else {
+    {
+      const PairIdx x = pair_idx<CC>(a, co);
+      col_transform<P, SRC, MODE, NV, LN>(a, x.ca, x.valid, x.field, x.base, x.tau, x.c, C, nthr, sm, v, cg);
+    }
+    float2* stash = sm + (size_t)spad(N) * C + co.tid();
+#pragma unroll
+    for (int q = 0; q < P; ++q) stash[q * nthr] = v[q];
+    {
+      // pair M/2 is one column: its second transform only keeps the CTA's
+      // barriers in step (an in-place pass has already replaced its input)
+      const PairIdx x = pair_idx<CC>(a, co);
+      col_transform<P, SRC, MODE, NV, LN>(a, x.cb, x.valid && x.ca != x.cb, x.field, x.base, x.tau, x.c, C, nthr,
+                                          sm, v, cg);
+    }
   }
   const PairIdx x = pair_idx<CC>(a, co);
   if (!x.valid) return;
   float2* out = a.out + x.base;
   const float2 w = __ldg(a.twz + x.p);
-  stash = sm + (size_t)spad(N) * C + co.tid();
+  const float2* stash = sm + (size_t)spad(N) * C + co.tid();
 #pragma unroll
   for (int q = 0; q < P; ++q) {
     const int64_t oa = col_offset(a, x.tau + TPT * q, x.ca);
