@@ -31,7 +31,10 @@ SCHEDS_2D = [(1, 16, 1, 16, 1, 16, 1, 1), (8, 8, 2, 16, 1, 8, 4, 1), (4, 4, 4, 1
              (16, 16, 4, 16, 1, 16, 2, 4), (2, 8, 1, 16, 1, 4, 1, 1),
              # c2r pass fed by bulk copies: tile T = C, T < C, T = 1, pipelined
              (2, 16, 1, 16, 1, 16, 2, 1, 1), (4, 8, 2, 16, 1, 8, 8, 1, 1), (1, 16, 1, 16, 1, 4, 4, 1, 1),
-             (16, 16, 4, 16, 1, 16, 16, 2, 1), (8, 16, 2, 16, 1, 16, 8, 4, 1)]
+             (16, 16, 4, 16, 1, 16, 16, 2, 1), (8, 16, 2, 16, 1, 16, 8, 4, 1),
+             # 256-thread radix-16 geometries (C N = 4096): the compile-time forms of
+             # the noise pass (N_1 = 256, 16 column pairs) and the c2r pass (M = 256, 16 rows)
+             (2, 16, 16, 16, 1, 16, 16, 1, 0), (16, 16, 16, 16, 1, 16, 16, 1, 0)]
 
 
 @pytest.mark.parametrize("sched", SCHEDS_2D)
@@ -133,3 +136,25 @@ def test_tune_keeps_a_cached_schedule(tmp_path):
         assert path.read_text().count("\n") == 1  # nothing re-timed or stored
     finally:
         del os.environ["GRF_TUNE_CACHE"]
+
+
+def test_forced_compile_time_geometries_3d(tmp_path):
+    """3-D schedule whose noise pass (N_1 = 256, 16 columns) and c2r pass
+    (M = 128, 32 rows) take the compile-time forms, with the axis-2 pair pass
+    at 16 points (N_2 = 16, general form): fields match the oracle."""
+    from paper_1105_2737_gb300 import api
+    shape, Lb, batch = (256, 16, 256), (1.0, 1.0, 1.0), 2
+    sched = (1, 16, 16, 16, 16, 16, 32, 1, 0)
+    path = tmp_path / "tune.txt"
+    path.write_text(_key2(shape, 2, batch) + " " + " ".join(str(v) for v in sched) + "\n")
+    os.environ["GRF_TUNE_CACHE"] = str(path)
+    try:
+        g = api.GRF(shape, Lb, ell=0.05, nu=1.5, max_batch=batch)
+    finally:
+        del os.environ["GRF_TUNE_CACHE"]
+    sch = g.schedule
+    assert (sch["colA_P"], sch["colA_C"], sch["row_P"], sch["row_C"]) == (16, 16, 16, 32)
+    f = g.sample(seed=13, batch=batch).cpu().numpy()
+    ref = O.sample(shape, Lb, O.Spectrum(O.MATERN, 1.0, 0.05, 1.5), 13, batch)
+    rel = np.linalg.norm(f - ref) / np.linalg.norm(ref)
+    assert rel <= 2e-6 and np.abs(f - ref).max() <= 1e-5 * np.sqrt((ref ** 2).mean()), rel
