@@ -267,6 +267,20 @@ grf_status grf_batch_set_debug(grf_plan p, int withhold_field, double timeout_ms
 grf_status grf_status_word(grf_plan p, void* stream);
 
 /*
+ * grf_cov_origin - the Monte Carlo covariance estimator of the paper's 1-D
+ * study (§4): samples the fields seed, seed + 1, ..., seed + count - 1 of a
+ * 1-D FP32 plan (in chunks of max_batch, exactly as grf_sample would) and adds
+ *   sums[j] += sum_b f_b(x_0) f_b(x_j),   j = 0 .. N_1 - 1,
+ * where x_0 is the origin of the grid; Cov(x_j) = sums[j] / count.  FP64
+ * sums, added in a fixed order (the result does not depend on scheduling).
+ *   sums : device pointer, N_1 doubles, caller-owned (zero it before the
+ *          first call; later calls keep adding).
+ * The plan keeps one chunk of fields and its partial sums (allocated on the
+ * first call).  GRF_ERR_UNSUPPORTED for a plan that is not 1-D FP32.
+ */
+grf_status grf_cov_origin(grf_plan p, uint64_t seed, int64_t count, double* sums, void* stream);
+
+/*
  * grf_philox_words - the raw generator behind R() of §3 Algorithms 1 and 2:
  * Philox4x32-10 words of calls q0 .. q0 + count - 1 with counter
  * (q_lo, q_hi, tag, 0) and key (lo, hi) of `key`, written as 4 uint32 per call

@@ -66,6 +66,7 @@ def lib():
             "grf_status_word": (C.c_int, [P, VP]),
             "grf_batch_set_debug": (C.c_int, [P, C.c_int, C.c_double]),
             "grf_philox_words": (C.c_int, [U64, C.c_uint32, U64, I64, VP, VP]),
+            "grf_cov_origin": (C.c_int, [P, U64, I64, VP, VP]),
             "grf_sample_2d_static": (C.c_int, [C.POINTER(I64), C.POINTER(D), C.POINTER(grf_spectrum), U64, I64,
                                                VP, VP]),
             "grf_plan_query": (I64, [P, C.c_int]),
@@ -185,6 +186,11 @@ def grf_status_word(plan, stream=0) -> int:
 def grf_philox_words(key, tag, q0, count, out_ptr, stream=0):
     check(lib().grf_philox_words(C.c_uint64(key & 0xFFFFFFFFFFFFFFFF), C.c_uint32(tag), C.c_uint64(q0), int(count),
                                  C.c_void_p(out_ptr), C.c_void_p(stream)), "grf_philox_words")
+
+
+def grf_cov_origin(plan, seed, count, sums_ptr, stream=0):
+    check(lib().grf_cov_origin(plan, C.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), int(count), C.c_void_p(sums_ptr),
+                               C.c_void_p(stream)), "grf_cov_origin")
 
 
 def grf_sample_2d_static(n, L, spec, seed, batch, out_ptr, stream=0):

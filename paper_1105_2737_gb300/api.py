@@ -104,6 +104,16 @@ class GRF:
             L.grf_backward(self.handle, int(seed), batch, grad_out.data_ptr(), gp.data_ptr(), _stream_ptr(self.device))
         return gp
 
+    def cov_origin(self, seed: int, count: int, sums: torch.Tensor | None = None) -> torch.Tensor:
+        """The estimator of the paper's 1-D study: sums[j] (+)= sum_b f_b(0) f_b(x_j)
+        over the fields seed .. seed + count - 1 (float64, on the device).
+        Cov(x_j) = sums[j] / count.  1-D FP32 plans."""
+        if sums is None:
+            sums = torch.zeros(self.shape[0], dtype=torch.float64, device=self.device)
+        with torch.cuda.device(self.device):
+            L.grf_cov_origin(self.handle, int(seed), int(count), sums.data_ptr(), _stream_ptr(self.device))
+        return sums
+
     def rfft(self, x: torch.Tensor) -> torch.Tensor:
         """Forward real-to-complex DFT of real fields onto the half spectrum (complex64)."""
         x = x.contiguous().to(self.dtype)

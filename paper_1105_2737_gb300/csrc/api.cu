@@ -181,6 +181,10 @@ struct grf_plan_s {
 
   int* status = nullptr;  // device status word
 
+  // 1-D covariance estimator (grf_cov_origin): one chunk of fields and its partial sums
+  float* cov_buf = nullptr;
+  double* cov_partial = nullptr;
+
   BatchPlan* batch = nullptr;
 
   // per-launch timing
@@ -217,6 +221,8 @@ void free_plan(grf_plan p) {
       if (p->ev_part[j][i]) cudaEventDestroy(p->ev_part[j][i]);
   }
   cudaFree(p->status);
+  cudaFree(p->cov_buf);
+  cudaFree(p->cov_partial);
   if (p->batch) batch_plan_free(p->batch);
   for (cudaEvent_t e : p->tev) cudaEventDestroy(e);
   delete p;
@@ -1137,6 +1143,29 @@ grf_status grf_status_word(grf_plan p, void* stream) {
   GRF_CUDA(cudaMemcpy(&h, p->status, sizeof(int), cudaMemcpyDeviceToHost), "status read");
   GRF_CUDA(cudaMemset(p->status, 0, sizeof(int)), "status clear");
   return (grf_status)h;
+}
+
+grf_status grf_cov_origin(grf_plan p, uint64_t seed, int64_t count, double* sums, void* stream) {
+  grf_status st = check_plan(p);
+  if (st != GRF_OK) return st;
+  if (p->kind != 0 || p->d != 1 || p->prec != GRF_FP32)
+    return fail(GRF_ERR_UNSUPPORTED, "grf_cov_origin needs a 1-D FP32 plan");
+  if (count < 1) return fail(GRF_ERR_INVALID_ARG, "count must be >= 1");
+  if (!sums) return fail(GRF_ERR_INVALID_ARG, "sums is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int N = (int)p->n[0];
+  const int64_t chunk = std::min<int64_t>(p->max_batch, (int64_t)65535 * 64);
+  if (!p->cov_buf) {
+    GRF_CUDA(dmalloc(&p->cov_buf, (size_t)(chunk * N)), "estimator field buffer");
+    GRF_CUDA(dmalloc(&p->cov_partial, (size_t)(cov_origin_partial_count(chunk) * N)), "estimator partial sums");
+  }
+  for (int64_t f0 = 0; f0 < count; f0 += chunk) {
+    const int64_t nb = std::min(chunk, count - f0);
+    st = grf_sample(p, seed + (uint64_t)f0, nb, p->cov_buf, stream);
+    if (st != GRF_OK) return st;
+    LAUNCH(launch_cov_origin(p->cov_buf, nb, N, p->cov_partial, sums, s), "covariance estimator");
+  }
+  return GRF_OK;
 }
 
 grf_status grf_philox_words(uint64_t key, uint32_t tag, uint64_t q0, int64_t count, uint32_t* out_words,

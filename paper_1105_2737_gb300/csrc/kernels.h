@@ -131,6 +131,11 @@ size_t col_pair_smem_bytes(int N, int C);  // pair mode (ColArgs::zpair)
 bool c2r_tma_ok(const RowArgs& a);
 size_t c2r_tma_slot_bytes(int M, int C);
 cudaError_t launch_row_c2r_tma(int P, const RowArgs& a, int ctas_per_sm, int num_sms, int* status, cudaStream_t s);
+// The Monte Carlo covariance estimator of the 1-D study (study.cu): adds
+// sum_b f[b][0] f[b][j] (b < B, j < N) onto sums[j] in FP64, through
+// `partial` (cov_origin_partial_count(B) x N doubles).
+int64_t cov_origin_partial_count(int64_t B);
+cudaError_t launch_cov_origin(const float* f, int64_t B, int N, double* partial, double* sums, cudaStream_t s);
 // Launch bounds of the transform kernels: 256 threads per CTA for radix 16
 // (3 CTAs per SM), 512 for radix 8 (N = 4096 needs 512 threads of 8 points),
 // 1024 for radix 4 and below.

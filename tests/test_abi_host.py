@@ -80,6 +80,7 @@ def test_invalid_parameters(L):
     assert st == 1
     assert L.lib().grf_plan_create(None, 2, None, None, None, 2, 0, 1) == 1
     assert L.lib().grf_sample(None, 0, 1, None, None) == 1
+    assert L.lib().grf_cov_origin(None, 0, 1, None, None) == 1
     assert L.lib().grf_plan_destroy(None) == 0
     assert L.lib().grf_plan_query(None, 0) == -1
 
