@@ -18,6 +18,8 @@ What it computes, per field (paper section in brackets):
   spectrum H (k_d = 0..N_d/2) and one inverse DFT                    [§2 Lemma 1, Eq. conj, §3 Alg. 2]
 * Algorithm 1: real noise -> forward DFT -> scale -> inverse DFT     [§2 Eq. 1, §3 Alg. 1]
 * exact covariance c(r) = (1/|D|) sum_K S(p_K) cos(2 pi K.r/N)      [§2, consequence of rules a)-d)]
+* Neumann / Dirichlet fields by cosine / sine sums on the mirrored box,
+  with the method-of-images covariance                              [§1, §3 remark on DCT/DST]
 * the radially binned power-spectrum loss and its analytic gradient
   with respect to (sigma, ell, nu) (no counterpart in the paper; the
   field's derivative follows from Eq. 2).
@@ -665,3 +667,159 @@ def rfft_halfspectrum(x: np.ndarray) -> np.ndarray:
     """DFT (exp(-)) of a real d-dimensional array, restricted to H."""
     M = x.shape[-1] // 2
     return dftn(x, -1)[..., : M + 1]
+
+
+# ---------------------------------------------------------------------------
+# Boundary-condition variants: cosine (Neumann) and sine (Dirichlet) transforms
+# ---------------------------------------------------------------------------
+#
+# §1 and §3 remark that the FFT may be replaced by the fast cosine or sine
+# transform, which gives fields with Neumann or Dirichlet boundary conditions;
+# the paper gives no formulas.  The reading fixed here:
+#
+# * the box [0, L_1] x ... x [0, L_d] carries N_i intervals per axis (N_i a
+#   power of two), i.e. the N_i + 1 points x_j = j L_i / N_i, j = 0..N_i;
+# * the spectral density is sampled on the frequencies of the mirrored box of
+#   edges 2 L_i (the even or odd extension of the field is periodic there):
+#   p_K = (k_i / (2 L_i))_i, k_i = 0..N_i, and S(p_K) / |2D|, |2D| = prod 2 L_i;
+# * Neumann: f_J = sum_{K in prod{0..N_i}} sqrt(w_K S(p_K)/|2D|) a_K prod_i cos(pi k_i j_i / N_i),
+#   w_K = prod_i w(k_i), w = 1 at k in {0, N}, 2 inside (the number of points
+#   of the mirrored grid that k stands for);
+# * Dirichlet: the same with sin(pi k_i j_i / N_i) and K over the interior
+#   prod{1..N_i-1} (w_K = 2^d); f vanishes on the boundary faces;
+# * a_K are independent N(0,1) reals; with the flat row-major index j of K in
+#   the (N_1+1) x ... x (N_d+1) grid: call j >> 2, counter (q_lo, q_hi, 2, 0),
+#   words 2t, 2t+1 with t = (j & 3) >> 1, even j the cosine normal of
+#   Box-Muller, odd j the sine normal (Algorithm 1's mapping with tag 2).
+# The covariance of either field is then the method-of-images sum of the
+# periodic covariance c of the mirrored grid (2 N_i points, period 2 L_i):
+#   Cov(f_J, f_J') = 2^-d sum_{sigma in {+1,-1}^d} sgn(sigma) c(J + sigma J'),
+# sgn = 1 (Neumann) or prod_i (-sigma_i) (Dirichlet); the tests pin the oracle
+# to that identity.
+
+BC_NEUMANN = 1
+BC_DIRICHLET = 2
+TAG_BC = 2
+
+
+def bc_shape(n: Sequence[int]):
+    """Points per axis of a boundary-condition field: N_i + 1."""
+    return tuple(int(x) + 1 for x in n)
+
+
+def bc_normals(n: Sequence[int], seed: int) -> np.ndarray:
+    """Real N(0,1) a_K on prod{0..N_i}: call j >> 2 (tag 2), pair (j & 3) >> 1, even j cos, odd j sin."""
+    shp = bc_shape(n)
+    ntot = int(np.prod(shp))
+    j = np.arange(ntot, dtype=np.uint64)
+    w = philox_words(j >> np.uint64(2), TAG_BC, seed)
+    t = ((j & np.uint64(3)) >> np.uint64(1)).astype(bool)
+    wa = np.where(t, w[2], w[0])
+    wb = np.where(t, w[3], w[1])
+    zr, zi = box_muller(wa, wb)
+    odd = (j & np.uint64(1)).astype(bool)
+    return np.where(odd, zi, zr).reshape(shp)
+
+
+def bc_axis_matrix(N: int, bc: int) -> np.ndarray:
+    """E[j, k] = cos(pi k j / N) (Neumann) or sin(pi k j / N) (Dirichlet), j, k = 0..N.
+
+    The angle is reduced exactly first: with m = k j mod 2N, pi k j / N = pi m / N
+    (mod 2 pi); the values at the quarter points m in {0, N/2, N, 3N/2} are
+    set to their exact 0 / +-1, so that the sine rows j in {0, N} vanish exactly."""
+    k = np.arange(N + 1, dtype=np.int64)
+    m = np.outer(k, k) % (2 * N)  # symmetric in (j, k)
+    ang = math.pi * m.astype(np.float64) / N
+    if bc == BC_NEUMANN:
+        E = np.cos(ang)
+        E[m == 0] = 1.0
+        E[m == N] = -1.0
+        if N % 2 == 0:
+            E[(m == N // 2) | (m == 3 * N // 2)] = 0.0
+    elif bc == BC_DIRICHLET:
+        E = np.sin(ang)
+        E[(m == 0) | (m == N)] = 0.0
+        if N % 2 == 0:
+            E[m == N // 2] = 1.0
+            E[m == 3 * N // 2] = -1.0
+    else:
+        raise ValueError("unknown boundary condition")
+    return E
+
+
+def bc_weights(n: Sequence[int], bc: int) -> np.ndarray:
+    """w_K on prod{0..N_i}: Neumann prod w(k_i) with w = 1 at {0, N}, 2 inside;
+    Dirichlet 2^d inside and 0 on the boundary."""
+    w = np.ones(bc_shape(n))
+    for i, N in enumerate(n):
+        wi = np.full(N + 1, 2.0)
+        wi[0] = wi[N] = 1.0 if bc == BC_NEUMANN else 0.0
+        shape = [1] * len(n)
+        shape[i] = N + 1
+        w = w * wi.reshape(shape)
+    return w
+
+
+def bc_scaled_density(n: Sequence[int], L: Sequence[float], spec: Spectrum) -> np.ndarray:
+    """S(p_K) / |2D| with p_K = (k_i / (2 L_i))_i, k_i = 0..N_i (the mirrored box)."""
+    if spec.normalize_discrete:
+        raise ValueError("normalize_discrete is not defined for boundary-condition fields")
+    axes = [np.arange(N + 1, dtype=np.float64) / (2.0 * Li) for N, Li in zip(n, L)]
+    p = np.meshgrid(*axes, indexing="ij")
+    vol2 = float(np.prod([2.0 * Li for Li in L]))
+    return spectral_density(p, spec) / vol2
+
+
+def bc_coefficients(n, L, spec: Spectrum, bc: int) -> np.ndarray:
+    """sqrt(w_K S(p_K) / |2D|), the factor in front of a_K."""
+    return np.sqrt(bc_weights(n, bc) * bc_scaled_density(n, L, spec))
+
+
+def bc_field_from_a(a: np.ndarray, n, L, spec: Spectrum, bc: int) -> np.ndarray:
+    """f_J = sum_K coef_K a_K prod_i E_i[j_i, k_i], one axis at a time (a dense
+    (N_i+1) x (N_i+1) matrix product per axis)."""
+    x = bc_coefficients(n, L, spec, bc) * a
+    for i, N in enumerate(n):
+        E = bc_axis_matrix(N, bc)
+        x = np.moveaxis(np.tensordot(E, x, axes=([1], [i])), 0, i)
+    return x
+
+
+def bc_field(n, L, spec: Spectrum, bc: int, seed: int) -> np.ndarray:
+    """One Neumann or Dirichlet field (seed is the per-field key)."""
+    return bc_field_from_a(bc_normals(n, seed), n, L, spec, bc)
+
+
+def bc_sample(n, L, spec: Spectrum, bc: int, seed: int, batch: int = 1) -> np.ndarray:
+    """batch fields; field b uses key seed + b."""
+    return np.stack([bc_field(n, L, spec, bc, (seed + b) & 0xFFFFFFFFFFFFFFFF) for b in range(batch)])
+
+
+def bc_field_lines(n, L, spec: Spectrum, bc: int, seed: int, lead_index_list) -> np.ndarray:
+    """Selected lines f[j_1, ..., j_{d-1}, :] of one field, by the same sums:
+    for each chosen (j_1..j_{d-1}) the sums over k_1..k_{d-1} contract against
+    the rows E_i[j_i, :], then the last axis is a dense matrix product."""
+    x = bc_coefficients(n, L, spec, bc) * bc_normals(n, seed)
+    Ed = bc_axis_matrix(n[-1], bc)
+    out = []
+    for J in lead_index_list:
+        line = x
+        for i in range(len(n) - 1):
+            line = np.tensordot(bc_axis_matrix(n[i], bc)[J[i]], line, axes=([0], [0]))
+        out.append(Ed @ line)
+    return np.stack(out)
+
+
+def bc_exact_covariance(n, L, spec: Spectrum, bc: int, J, Jp) -> float:
+    """Cov(f_J, f_J') by the method of images on the mirrored periodic grid:
+    2^-d sum_sigma sgn(sigma) c(J + sigma J') with c = exact_covariance(2n, 2L)."""
+    d = len(n)
+    n2 = [2 * N for N in n]
+    c = exact_covariance(n2, [2.0 * Li for Li in L], spec)
+    acc = 0.0
+    for sig in np.ndindex(*([2] * d)):
+        s = [1 if t == 0 else -1 for t in sig]
+        lag = tuple((J[i] + s[i] * Jp[i]) % n2[i] for i in range(d))
+        sgn = 1.0 if bc == BC_NEUMANN else float(np.prod([-si for si in s]))
+        acc += sgn * c[lag]
+    return acc / 2 ** d
