@@ -435,6 +435,81 @@ def run_cov1d_study(args):
                               "a few times 1/sqrt(samples)"}), flush=True)
 
 
+def run_bc_study(args):
+    """Neumann / Dirichlet fields (the cosine / sine transform variant): fields/s,
+    Gpts/s and the HBM roofline of each pass at 2-D 4096^2 intervals (4097^2
+    points, batch 16) and 3-D 256^3 intervals (batch 4), with the periodic
+    plan of the same grid beside it and the FP64 oracle timed on one 2-D field.
+    Inputs (1 GB per 2-D batch) are larger than L2.  One JSON line."""
+    import torch
+    from paper_1105_2737_gb300 import build
+    build()
+    from paper_1105_2737_gb300 import _lib as L
+    from paper_1105_2737_gb300.api import GRF, GRFBoundary
+    hbm, peak_src = _peaks()
+    dev = torch.device("cuda", 0)
+    rows = []
+    cases = [((4096, 4096), 16, "neumann"), ((4096, 4096), 16, "dirichlet"), ((256, 256, 256), 4, "neumann")]
+    for n, batch, bc in cases:
+        g = GRFBoundary(n, [1.0] * len(n), bc=bc, max_batch=batch, **SPEC)
+        out = torch.empty((batch,) + g.shape, dtype=torch.float32, device=dev)
+        for w in range(3):
+            g.sample(w * batch, batch, out)
+        torch.cuda.synchronize()
+        steps = args.steps if args.steps <= 20 else 10
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k in range(steps):
+            g.sample((k + 3) * batch, batch, out)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        L.grf_plan_timing(g.handle, 16)
+        g.sample(0, batch, out)
+        torch.cuda.synchronize()
+        _, launches = L.grf_plan_timing_read(g.handle)
+        L.grf_plan_timing(g.handle, 0)
+        pts = batch * g.points
+        passes = []
+        for kind, t in launches:
+            byts = pts * 8  # noise pass: t_K read + field written; axis pass: field read + written
+            passes.append({"kind": kind, "ms": t, "bytes": byts, "gbs": byts / (t / 1e3) / 1e9,
+                           "frac": byts / (t / 1e3) / 1e9 / hbm})
+        g.close()
+        del out
+        # the periodic plan of the same grid, same batch, for context
+        gp = GRF(n, [1.0] * len(n), max_batch=batch, **SPEC)
+        outp = torch.empty((batch,) + tuple(n), dtype=torch.float32, device=dev)
+        for w in range(3):
+            gp.sample(w, batch, outp)
+        torch.cuda.synchronize()
+        e0.record()
+        for k in range(steps):
+            gp.sample(k, batch, outp)
+        e1.record()
+        torch.cuda.synchronize()
+        msp = e0.elapsed_time(e1) / steps
+        gp.close()
+        del outp
+        torch.cuda.empty_cache()
+        rows.append({"intervals": list(n), "bc": bc, "batch": batch, "ms_per_call": ms,
+                     "fields_per_s": batch / (ms / 1e3), "gpts_per_s": pts / (ms / 1e3) / 1e9,
+                     "passes": passes, "periodic_same_grid_fields_per_s": batch / (msp / 1e3)})
+    cpu = None
+    if not args.no_cpu:
+        from oracle import grf_oracle as O
+        sp = O.Spectrum(family=O.MATERN, sigma=SPEC["sigma"], ell=SPEC["ell"], nu=SPEC["nu"])
+        t0 = time.perf_counter()
+        O.bc_field((4096, 4096), (1.0, 1.0), sp, O.BC_NEUMANN, 0)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 1.0 / dt, "unit": "fields/s", "cores": torch.get_num_threads(), "kind": "oracle",
+               "sample": "one 4096^2-interval Neumann field, FP64 numpy oracle, %.1f s" % dt}
+    print(json.dumps({"study": "Neumann / Dirichlet fields (cosine / sine transforms)", "rows": rows,
+                      "roofline_peak_gbs": hbm, "peak_source": peak_src + " hbm_gbs (copy, burst)",
+                      "cpu_baseline": cpu,
+                      "note": "algorithmic bytes 8 per point per pass; batch > L2"}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -445,11 +520,14 @@ def main():
     ap.add_argument("--batch", type=int, default=BATCH, help="fields per step (profiling runs use a smaller batch)")
     ap.add_argument("--no-extras", action="store_true", help="skip the e2e, FP64 and 3-D legs")
     ap.add_argument("--no-tune", action="store_true", help="keep the default schedule (no tuning run)")
-    ap.add_argument("--study", choices=["cov1d"], help="run the paper's 1-D covariance study instead")
+    ap.add_argument("--study", choices=["cov1d", "bc"],
+                    help="run the paper's 1-D covariance study, or the Neumann / Dirichlet fields, instead")
     ap.add_argument("--study-samples", type=int, default=100_000_000)
     args = ap.parse_args()
     if args.study == "cov1d":
         run_cov1d_study(args)
+    elif args.study == "bc":
+        run_bc_study(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

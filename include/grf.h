@@ -92,6 +92,11 @@ typedef struct {
                             1: rescale S so that (1/|D|) sum_K S(p_K) = sigma^2 exactly */
 } grf_spectrum;
 
+typedef enum {
+  GRF_BC_NEUMANN = 1,  /* cosine transform: the field's mirror image across every face is smooth */
+  GRF_BC_DIRICHLET = 2 /* sine transform: the field vanishes on every face */
+} grf_boundary;
+
 typedef struct grf_plan_s* grf_plan;
 
 /*
@@ -118,6 +123,39 @@ typedef struct grf_plan_s* grf_plan;
  */
 grf_status grf_plan_create(grf_plan* out, int d, const int64_t* n, const double* L,
                            const grf_spectrum* spec, int alg, int prec, int64_t max_batch);
+
+/*
+ * grf_bc_plan_create - plan for fields with Neumann or Dirichlet boundary
+ * conditions: the variant that §1 and §3 mention, in which the FFT is replaced
+ * by the fast cosine or sine transform (the paper gives no formulas; this is
+ * the library's reading).  The box [0, L_1] x ... x [0, L_d] carries N_i
+ * intervals per axis, i.e. the points x_j = j L_i / N_i, j = 0..N_i, and a
+ * field is the (N_1 + 1) x ... x (N_d + 1) array (C order, FP32)
+ *   f_J = sum_K c_K a_K prod_i E(k_i, j_i),   J, K in prod{0..N_i},
+ *   E = cos(pi k j / N_i) (GRF_BC_NEUMANN) or sin(pi k j / N_i) (GRF_BC_DIRICHLET),
+ *   c_K = sqrt(w_K S(p_K) / |2D|),  p_K = (k_i / (2 L_i))_i,  |2D| = prod 2 L_i,
+ *   w_K = prod_i w(k_i): Neumann w = 1 for k in {0, N_i}, 2 otherwise;
+ *   Dirichlet w = 0 for k in {0, N_i}, 2 otherwise,
+ * a_K independent N(0, 1): with the flat row-major index j of K, Philox call
+ * j >> 2 with counter (q_lo, q_hi, 2, 0) and key seed + b, words 2t and 2t + 1
+ * (t = (j & 3) >> 1), the Box-Muller cosine normal for even j and the sine
+ * normal for odd j.  Its covariance is the method-of-images sum of the periodic
+ * covariance c of the mirrored grid (2 N_i points, period 2 L_i):
+ *   Cov(f_J, f_J') = 2^-d sum_{s in {+1,-1}^d} sgn(s) c(J + s J'),
+ * sgn = 1 (Neumann) or prod_i (-s_i) (Dirichlet); a Dirichlet field is exactly
+ * 0 on the faces.
+ *   n    : host array of d interval counts, powers of two in [2, 4096].
+ *   L    : host array of d edge lengths, each > 0.
+ *   spec : any family; normalize_discrete must be 0 (else GRF_ERR_UNSUPPORTED).
+ *   bc   : grf_boundary.
+ * grf_sample on the plan writes batch * prod (N_i + 1) floats; grf_plan_query
+ * answers keys 0 (points per field), 3..6 and 16 (bc); grf_plan_timing
+ * records its launches (GRF_KERNEL_R2R_NOISE, GRF_KERNEL_R2R).  The other
+ * calls return GRF_ERR_INVALID_ARG for such a plan.  The plan holds the
+ * FP64-computed, FP32-rounded c_K (prod (N_i + 1) floats) and the twiddles.
+ */
+grf_status grf_bc_plan_create(grf_plan* out, int d, const int64_t* n, const double* L,
+                              const grf_spectrum* spec, int bc, int64_t max_batch);
 
 /*
  * grf_plan_set_spectrum - rebuild the plan's spectral tables for new
@@ -308,7 +346,9 @@ enum {
   GRF_KERNEL_ROWS_R2C = 3,      /* r2c along the last axis */
   GRF_KERNEL_ROWS_1D = 4,       /* 1-D single-pass kernels */
   GRF_KERNEL_PLAIN64 = 5,       /* one field of the plain FP64 form (a launch sequence) */
-  GRF_KERNEL_REDUCE = 6         /* adjoint final sum */
+  GRF_KERNEL_REDUCE = 6,        /* adjoint final sum */
+  GRF_KERNEL_R2R_NOISE = 7,     /* boundary fields: noise + cosine / sine transform along the last axis */
+  GRF_KERNEL_R2R = 8            /* boundary fields: cosine / sine transform along a strided axis */
 };
 grf_status grf_plan_timing(grf_plan p, int64_t cap);
 int64_t grf_plan_timing_read(grf_plan p, int* kinds, float* ms, int64_t cap_out);
@@ -318,8 +358,9 @@ int64_t grf_plan_timing_read(grf_plan p, int* kinds, float* ms, int64_t cap_out)
  * 4..6 = N_1..N_3, 7 = tile T, 8/9 = radix and columns per CTA of the axis-1
  * pass, 10/11 = the same for the c2r pass, 12 = pipelining depth, 13/14 = the
  * axis-2 pass (3-D), 15 = 1 if the c2r pass is the persistent kernel fed by
- * bulk asynchronous copies (else the plain row kernel).  Returns -1 for an
- * unknown key or a NULL plan. */
+ * bulk asynchronous copies (else the plain row kernel), 16 = the boundary
+ * condition of a grf_bc_plan_create plan.  Returns -1 for an unknown key or a
+ * NULL plan. */
 int64_t grf_plan_query(grf_plan p, int key);
 
 /* grf_plan_destroy - free the plan and everything it owns (NULL is allowed). */

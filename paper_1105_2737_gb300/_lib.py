@@ -24,6 +24,8 @@ GRF_ALG_TWO_FFT = 1
 GRF_ALG_ONE_FFT = 2
 GRF_FP32 = 0
 GRF_FP64 = 1
+GRF_BC_NEUMANN = 1
+GRF_BC_DIRICHLET = 2
 
 
 class grf_spectrum(C.Structure):
@@ -53,6 +55,8 @@ def lib():
         sig = {
             "grf_plan_create": (C.c_int, [C.POINTER(P), C.c_int, C.POINTER(I64), C.POINTER(D),
                                           C.POINTER(grf_spectrum), C.c_int, C.c_int, I64]),
+            "grf_bc_plan_create": (C.c_int, [C.POINTER(P), C.c_int, C.POINTER(I64), C.POINTER(D),
+                                             C.POINTER(grf_spectrum), C.c_int, I64]),
             "grf_plan_set_spectrum": (C.c_int, [P, C.POINTER(grf_spectrum), VP]),
             "grf_plan_tune": (C.c_int, [P, VP]),
             "grf_sample": (C.c_int, [P, U64, I64, VP, VP]),
@@ -107,6 +111,15 @@ def grf_plan_create(d, n, L, spec, alg=GRF_ALG_ONE_FFT, prec=GRF_FP32, max_batch
     LL = (C.c_double * d)(*[float(x) for x in L])
     check(lib().grf_plan_create(C.byref(h), int(d), nn, LL, C.byref(spec), int(alg), int(prec), int(max_batch)),
           "grf_plan_create")
+    return h
+
+
+def grf_bc_plan_create(d, n, L, spec, bc, max_batch=1):
+    h = C.c_void_p()
+    nn = (C.c_int64 * d)(*[int(x) for x in n])
+    LL = (C.c_double * d)(*[float(x) for x in L])
+    check(lib().grf_bc_plan_create(C.byref(h), int(d), nn, LL, C.byref(spec), int(bc), int(max_batch)),
+          "grf_bc_plan_create")
     return h
 
 
@@ -206,7 +219,7 @@ def grf_plan_query(plan, key: int) -> int:
 
 
 KERNEL_KINDS = {0: "noise_columns", 1: "columns", 2: "rows_c2r", 3: "rows_r2c", 4: "rows_1d", 5: "plain64",
-                6: "reduce"}
+                6: "reduce", 7: "r2r_noise_rows", 8: "r2r_columns"}
 
 
 def grf_plan_timing(plan, cap):

@@ -140,6 +140,53 @@ class GRF:
             pass
 
 
+class GRFBoundary:
+    """Fields with Neumann or Dirichlet boundary conditions on [0, L_1] x ... x [0, L_d]
+    (the cosine / sine transform variant of the method): `intervals` N_i per axis,
+    fields of shape (N_1 + 1, ..., N_d + 1), FP32."""
+
+    def __init__(self, intervals: Sequence[int], lengths: Sequence[float] | None = None, bc: str = "neumann",
+                 family: str = "matern", sigma: float = 1.0, ell: float = 0.1, nu: float = 1.5, m: float = 1.0,
+                 k: int = 1, l: int = 1, n: int = 1, max_batch: int = 1, device=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("GRFBoundary needs a CUDA device; there is no CPU fallback")
+        self.intervals = tuple(int(s) for s in intervals)
+        self.d = len(self.intervals)
+        self.shape = tuple(s + 1 for s in self.intervals)
+        self.lengths = tuple(float(x) for x in (lengths if lengths is not None else [1.0] * self.d))
+        self.bc = {"neumann": L.GRF_BC_NEUMANN, "dirichlet": L.GRF_BC_DIRICHLET}[bc]
+        self.max_batch = int(max_batch)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else torch.device(device).index or 0)
+        spec = L.make_spectrum(_FAMILIES[family], sigma, ell, nu, m, k, l, n, 0)
+        with torch.cuda.device(self.device):
+            self.handle = L.grf_bc_plan_create(self.d, self.intervals, self.lengths, spec, self.bc, self.max_batch)
+
+    def sample(self, seed: int = 0, batch: int = 1, out: torch.Tensor | None = None) -> torch.Tensor:
+        """batch fields of shape (N_1 + 1, ..., N_d + 1); field b uses Philox key seed + b."""
+        if out is None:
+            out = torch.empty((batch,) + self.shape, dtype=torch.float32, device=self.device)
+        assert out.is_contiguous() and out.dtype == torch.float32 and out.device == self.device
+        assert out.numel() == batch * self.points
+        with torch.cuda.device(self.device):
+            L.grf_sample(self.handle, int(seed), int(batch), out.data_ptr(), _stream_ptr(self.device))
+        return out
+
+    @property
+    def points(self) -> int:
+        return L.grf_plan_query(self.handle, 0)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            L.grf_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class _GRFFields(torch.autograd.Function):
     @staticmethod
     def forward(ctx, theta: torch.Tensor, plan: GRF, seed: int, batch: int):

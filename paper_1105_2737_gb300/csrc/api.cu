@@ -187,6 +187,12 @@ struct grf_plan_s {
 
   BatchPlan* batch = nullptr;
 
+  // Neumann / Dirichlet fields (kind 2): n[] holds the intervals N_i, a field
+  // has prod (N_i + 1) points; t_K in field layout
+  int bc = 0;
+  float* bctab = nullptr;
+  int bcC[3] = {1, 1, 1};  // sequences per CTA of the pass along each axis
+
   // per-launch timing
   std::vector<cudaEvent_t> tev;
   std::vector<int> tkind;
@@ -199,6 +205,7 @@ void free_plan(grf_plan p) {
   if (!p) return;
   cudaFree(p->tw);
   cudaFree(p->stab);
+  cudaFree(p->bctab);
   cudaFree(p->dstab);
   cudaFree(p->ws);
   cudaFree(p->partial);
@@ -566,7 +573,103 @@ namespace grf {
 void set_last_error(const char* msg) { g_last_error = msg; }
 }  // namespace grf
 
+namespace {
+
+// Neumann / Dirichlet fields: the noise + last-axis launch, then one in-place
+// launch per remaining axis, from the last but one to the first.
+grf_status sample_bc(grf_plan p, uint64_t seed, int64_t batch, float* out, cudaStream_t s) {
+  if (!out) return fail(GRF_ERR_INVALID_ARG, "out is NULL");
+  if (batch < 1 || batch > p->max_batch) return fail(GRF_ERR_INVALID_ARG, "batch must be in [1, max_batch]");
+  const int d = p->d;
+  int64_t pts[3] = {1, 1, 1};
+  for (int i = 0; i < d; ++i) pts[i] = p->n[i] + 1;
+  for (int ax = d - 1; ax >= 0; --ax) {
+    R2rArgs a{};
+    a.f = out;
+    a.field_stride = p->ntot;
+    a.lines_per_field = p->ntot / pts[ax];
+    a.nlines = batch * a.lines_per_field;
+    a.inner = 1;
+    for (int i = ax + 1; i < d; ++i) a.inner *= pts[i];
+    a.N = (int)p->n[ax];
+    a.logNF = ilog2(2 * p->n[ax]);
+    a.C = p->bcC[ax];
+    a.logC = ilog2(a.C);
+    a.logG = a.logC + 1;
+    a.bc = p->bc;
+    a.d = d;
+    a.axis = ax;
+    for (int i = 0; i < 3; ++i) a.pts[i] = pts[i];
+    a.noise = ax == d - 1;
+    a.tab = p->bctab;
+    a.seed = seed;
+    a.field0 = 0;
+    a.tw = p->tw + 2 * p->n[ax];
+    a.tws = p->tw + 2 * p->twmax;
+    a.trig = p->tw + 256;
+    TLAUNCH(a.noise ? GRF_KERNEL_R2R_NOISE : GRF_KERNEL_R2R, launch_r2r(a, s),
+            a.noise ? "boundary field: noise + last axis" : "boundary field: axis pass");
+  }
+  return GRF_OK;
+}
+
+}  // namespace
+
 extern "C" {
+
+grf_status grf_bc_plan_create(grf_plan* out, int d, const int64_t* n, const double* L, const grf_spectrum* spec,
+                              int bc, int64_t max_batch) {
+  g_last_error.clear();
+  if (!out) return fail(GRF_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (d < 1 || d > 3) return fail(GRF_ERR_INVALID_ARG, "d must be 1, 2 or 3");
+  if (!n || !L) return fail(GRF_ERR_INVALID_ARG, "n or L is NULL");
+  grf_status st = validate_spec(spec);
+  if (st != GRF_OK) return st;
+  if (bc != GRF_BC_NEUMANN && bc != GRF_BC_DIRICHLET) return fail(GRF_ERR_INVALID_ARG, "bc must be 1 or 2");
+  if (max_batch < 1 || max_batch > 65535) return fail(GRF_ERR_INVALID_ARG, "max_batch must be in [1, 65535]");
+  for (int i = 0; i < d; ++i) {
+    if (n[i] < 2) return fail(GRF_ERR_INVALID_ARG, "every N_i must be >= 2");
+    if (!(L[i] > 0) || !std::isfinite(L[i])) return fail(GRF_ERR_INVALID_ARG, "every L_i must be > 0");
+  }
+  if (spec->normalize_discrete) return fail(GRF_ERR_UNSUPPORTED, "normalize_discrete is for periodic plans");
+  int64_t ntot = 1;
+  for (int i = 0; i < d; ++i) {
+    if (!is_pow2(n[i]) || n[i] > 4096) return fail(GRF_ERR_UNSUPPORTED, "N_i must be a power of two <= 4096");
+    ntot *= n[i] + 1;
+  }
+  grf_plan p = new (std::nothrow) grf_plan_s();
+  if (!p) return fail(GRF_ERR_OOM, "host allocation");
+  p->kind = 2;
+  p->d = d;
+  for (int i = 0; i < d; ++i) {
+    p->n[i] = n[i];
+    p->L[i] = L[i];
+  }
+  p->spec = *spec;
+  p->prec = GRF_FP32;
+  p->max_batch = max_batch;
+  p->bc = bc;
+  p->ntot = ntot;
+  cudaGetDevice(&p->device);
+  int64_t maxlen = 256;  // the length-256 table also serves Box-Muller's coarse angles
+  for (int i = 0; i < d; ++i) maxlen = std::max<int64_t>(maxlen, 2 * n[i]);
+  p->twmax = (int)maxlen;
+  for (int i = 0; i < d; ++i) p->bcC[i] = r2r_lines_per_cta((int)n[i]);
+  cudaError_t e;
+  if ((e = dmalloc(&p->status, 1)) != cudaSuccess || (e = cudaMemset(p->status, 0, sizeof(int))) != cudaSuccess ||
+      (e = dmalloc(&p->tw, 2 * maxlen + kStageTableEntries)) != cudaSuccess ||
+      (e = build_twiddles(p->tw, (int)maxlen, nullptr)) != cudaSuccess || (e = dmalloc(&p->bctab, ntot)) != cudaSuccess ||
+      (e = build_bc_table(p->bctab, spec_params(p), bc, nullptr)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(nullptr)) != cudaSuccess) {
+    grf_status r = cuda_fail(e, "boundary plan tables");
+    free_plan(p);
+    return r;
+  }
+  *out = p;
+  return GRF_OK;
+}
+
 
 const char* grf_status_string(grf_status s) {
   switch (s) {
@@ -732,6 +835,7 @@ grf_status grf_plan_set_spectrum(grf_plan p, const grf_spectrum* spec, void* str
 grf_status grf_sample(grf_plan p, uint64_t seed, int64_t batch, void* out, void* stream) {
   grf_status st = check_plan(p);
   if (st != GRF_OK) return st;
+  if (p->kind == 2) return sample_bc(p, seed, batch, (float*)out, (cudaStream_t)stream);
   if (p->kind != 0) return fail(GRF_ERR_INVALID_ARG, "batch plans use grf_batch_sample");
   if (!out) return fail(GRF_ERR_INVALID_ARG, "out is NULL");
   if (batch < 1 || batch > p->max_batch) return fail(GRF_ERR_INVALID_ARG, "batch must be in [1, max_batch]");
@@ -1211,6 +1315,17 @@ int64_t grf_plan_query(grf_plan p, int key) {
   if (p->kind == 1) {
     if (key == 0) return batch_plan_total_points(p->batch);
     return -1;
+  }
+  if (p->kind == 2) {
+    switch (key) {
+      case 0: return p->ntot;
+      case 3: return p->d;
+      case 4: return p->n[0];
+      case 5: return p->n[1];
+      case 6: return p->n[2];
+      case 16: return p->bc;
+      default: return -1;
+    }
   }
   switch (key) {
     case 0: return p->ntot;

@@ -75,7 +75,9 @@ cudaError_t prepare_kernel(const void* k, int threads, size_t smem) {
   while (need > cap && blocks > 1) need = per * --blocks;
   int pct = (int)((need * 100 + cap - 1) / cap);
   pct = pct < 0 ? 0 : (pct > 100 ? 100 : pct);
-  if (smem > 48 * 1024) {
+  // the limit is a property of the kernel, not of the launch shape: raise it,
+  // never lower it under a larger shape launched (and cached) before
+  if (smem > 48 * 1024 && (int)smem > fa.maxDynamicSharedSizeBytes) {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }

@@ -107,6 +107,34 @@ struct FourStepArgs {
 };
 cudaError_t launch_fourstep(int stage, int P, const FourStepArgs& a, int64_t nfields, cudaStream_t s);
 
+// One axis of a Neumann / Dirichlet field (r2r.cu): lines of N + 1 points
+// (N a power of two in [2, 4096]) along an axis of the field array, lines
+// (o, i) starting at o (N + 1) inner + i within a field; C complex sequences
+// (2C lines) per CTA, C * 2N / points_per_thread <= 512 threads.
+struct R2rArgs {
+  float* f;                 // the batch of fields, transformed in place
+  int64_t field_stride;     // points per field
+  int64_t nlines;           // lines over the batch
+  int64_t lines_per_field;
+  int64_t inner;            // stride between the points of a line (1: contiguous rows)
+  int N, logNF;             // intervals per line; log2 of the FFT length 2N
+  int C, logC, logG;        // sequences per CTA, log2 C, log2 (2C)
+  int bc;                   // 1: Neumann (cosine), 2: Dirichlet (sine)
+  int d, axis;              // dimension and the axis of this launch
+  int64_t pts[3];           // points per axis, N_i + 1
+  int noise;                // 1: draw a_K t_K (contiguous rows only) instead of loading
+  const float* tab;         // t_K, field layout (noise launch only)
+  uint64_t seed;            // key of field b is seed + field0 + b
+  int64_t field0;
+  const float2* tw;         // exp(2 pi i k / 2N), k < 2N
+  const float2* tws;        // radix-16 stage tables (see fft_core)
+  const float2* trig;       // exp(2 pi i h / 256): coarse angles of Box-Muller
+};
+cudaError_t launch_r2r(const R2rArgs& a, cudaStream_t s);
+size_t r2r_smem_bytes(int N, int C);
+int r2r_points_per_thread(int N);
+int r2r_lines_per_cta(int N);  // the default C for lines of N + 1 points
+
 // Host launchers (fft_kernels.cu).  P is the points per thread of the
 // transform (16 if the length is >= 16, else the length itself).
 cudaError_t launch_col(int src, int mode, int P, const ColArgs& a, dim3 grid, cudaStream_t s);
@@ -167,6 +195,11 @@ cudaError_t build_twiddles_d(double2* tw, int maxlen, cudaStream_t s);
 cudaError_t build_stab(float* stab, float* dstab, const SpecParams& sp, double dig_a_minus_nu,
                        cudaStream_t s);
 cudaError_t build_stab_d(double* stab, const SpecParams& sp, cudaStream_t s);
+// t_K of a Neumann (bc = 1) / Dirichlet (bc = 2) field on prod{0..N_i} in
+// field layout (last axis fastest): sqrt(S(p_K) / |2D|) with p_K = (k_i / (2 L_i))_i,
+// times 1 (k_i in {0, N_i}, Neumann), 0 (k_i in {0, N_i}, Dirichlet) or
+// 1/sqrt(2) (interior k_i) per axis.  sp.nn holds the intervals N_i.
+cudaError_t build_bc_table(float* tab, const SpecParams& sp, int bc, cudaStream_t s);
 cudaError_t philox_words(uint64_t key, uint32_t tag, uint64_t q0, int64_t count, uint32_t* out, cudaStream_t s);
 cudaError_t reduce_partials(const double* partial, int64_t nblk_per_field, int64_t nfields,
                             double* out, cudaStream_t s);

@@ -200,6 +200,49 @@ cudaError_t build_stab_d(double* stab, const SpecParams& sp, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// t_K of the boundary-condition fields: the folded-table machinery with the
+// table dimensions mapped so that the last axis is fastest (field layout), the
+// edges doubled (the mirrored box), and the per-axis factor of the extension.
+__global__ void bc_table_kernel(float* tab, DevSpec sp, int bc, int64_t total) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  double S, dl, dn;
+  spectral_entry(sp, i, &S, &dl, &dn);
+  const int f[3] = {(int)(i % sp.F[0]), (int)((i / sp.F[0]) % sp.F[1]), (int)(i / ((int64_t)sp.F[0] * sp.F[1]))};
+  double u = 1.0;
+  for (int t = 0; t < 3; ++t) {
+    if (sp.axis_of[t] < 0) continue;
+    const bool edge = f[t] == 0 || f[t] == sp.F[t] - 1;
+    u *= edge ? (bc == 1 ? 1.0 : 0.0) : 0.70710678118654752440;
+  }
+  tab[i] = (float)(sqrt(S) * u);
+}
+
+cudaError_t build_bc_table(float* tab, const SpecParams& sp, int bc, cudaStream_t s) {
+  SpecParams s2 = sp;
+  for (int i = 0; i < sp.d; ++i) s2.L[i] = 2.0 * sp.L[i];
+  DevSpec d = make_devspec(s2, 0.0);
+  // table dimension 0 (fastest) <-> the last axis, 1 <-> axis 2 of a 3-D
+  // grid, 2 <-> axis 1; N_i + 1 entries each
+  for (int t = 0; t < 3; ++t) {
+    d.F[t] = 1;
+    d.axis_of[t] = -1;
+  }
+  d.F[0] = sp.nn[sp.d - 1] + 1;
+  d.axis_of[0] = sp.d - 1;
+  if (sp.d == 3) {
+    d.F[1] = sp.nn[1] + 1;
+    d.axis_of[1] = 1;
+  }
+  if (sp.d >= 2) {
+    d.F[2] = sp.nn[0] + 1;
+    d.axis_of[2] = 0;
+  }
+  const int64_t total = (int64_t)d.F[0] * d.F[1] * d.F[2];
+  bc_table_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(tab, d, bc, total);
+  return cudaGetLastError();
+}
+
 // out[f * 3 + t] = sum_i partial[(f * nblk + i) * 3 + t], summed in index order.
 __global__ void reduce_partials_kernel(const double* partial, int64_t nblk, int64_t nfields, double* out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -92,3 +92,31 @@ def test_no_device_is_reported_not_crashed(L):
     st, h = _create(L, 2, [8, 8], [1.0, 1.0])
     assert st in (3, 4)  # CUDA error, reported as a status
     assert L.lib().grf_last_error()
+
+
+def _create_bc(L, d, n, Ls, bc=1, spec=None, max_batch=1):
+    h = C.c_void_p()
+    nn = (C.c_int64 * max(d, 1))(*n) if n is not None else None
+    LL = (C.c_double * max(d, 1))(*Ls) if Ls is not None else None
+    sp = spec if spec is not None else L.make_spectrum()
+    return L.lib().grf_bc_plan_create(C.byref(h), d, nn, LL, C.byref(sp), bc, max_batch), h
+
+
+@pytest.mark.parametrize("d,n,Ls,bc,status", [
+    (0, [4], [1.0], 1, 1),
+    (2, [4, 1], [1.0, 1.0], 1, 1),      # fewer than 2 intervals
+    (2, [4, 4], [1.0, 0.0], 2, 1),      # non-positive L
+    (2, [4, 4], [1.0, 1.0], 3, 1),      # unknown boundary condition
+    (2, [6, 4], [1.0, 1.0], 1, 2),      # not a power of two
+    (1, [8192], [1.0], 2, 2),           # above 4096 intervals
+])
+def test_boundary_plan_rejects_bad_arguments(L, d, n, Ls, bc, status):
+    st, h = _create_bc(L, d, n, Ls, bc=bc)
+    assert st == status
+    assert not h.value
+
+
+def test_boundary_plan_rejects_discrete_normalisation(L):
+    st, h = _create_bc(L, 2, [8, 8], [1.0, 1.0], spec=L.make_spectrum(normalize_discrete=1))
+    assert st == 2 and not h.value
+    assert L.lib().grf_bc_plan_create(None, 1, None, None, None, 1, 1) == 1
