@@ -165,7 +165,10 @@ __host__ __device__ constexpr int stage_table_offset() {
 //   nthr: threads taking part (C * N / P), the barrier count of every exchange
 // Every exchange starts with a barrier, so the caller may have used `sm` just
 // before; after return other threads may still read `sm`.
-template <int P, int DIR>
+// PF: load the next stage's twiddles before the exchange (latency hidden
+// behind it, P - 1 more live float2); without, load them after it (fewer
+// registers, for kernels held to 64 registers).
+template <int P, int DIR, bool PF = true>
 GRF_DEV void fft_core(float2 (&v)[P], float2* sm, int tau, int c, int C, int N, int logN,
                       const float2* __restrict__ tw, const float2* __restrict__ tws, int nthr) {
   if constexpr (P == 1) {
@@ -187,18 +190,28 @@ GRF_DEV void fft_core(float2 (&v)[P], float2* sm, int tau, int c, int C, int N, 
     const float2* tab = tws + stage_table_offset<P>();
     int Ns = 1;
     int off = 0;
-    float2 w[P - 1];  // twiddles of the next stage, loaded one stage ahead
+    float2 w[PF ? P - 1 : 1];  // twiddles of the next stage, loaded one stage ahead
     for (int s = 0; s < nP; ++s) {
       const int m = tau & (Ns - 1);
-      if (Ns > 1) {
+      if constexpr (PF) {
+        if (Ns > 1) {
 #pragma unroll
-        for (int r = 1; r < P; ++r) v[r] = cmul(v[r], make_float2(w[r - 1].x, DIR > 0 ? w[r - 1].y : -w[r - 1].y));
-      }
-      if (s + 1 < nP) {  // span of the next stage: P Ns
-        const float2* t = tab + off + (tau & (P * Ns - 1));
+          for (int r = 1; r < P; ++r) v[r] = cmul(v[r], make_float2(w[r - 1].x, DIR > 0 ? w[r - 1].y : -w[r - 1].y));
+        }
+        if (s + 1 < nP) {  // span of the next stage: P Ns
+          const float2* t = tab + off + (tau & (P * Ns - 1));
 #pragma unroll
-        for (int r = 1; r < P; ++r) w[r - 1] = __ldg(t + (r - 1) * (P * Ns));
-        off += (P - 1) * P * Ns;
+          for (int r = 1; r < P; ++r) w[r - 1] = __ldg(t + (r - 1) * (P * Ns));
+          off += (P - 1) * P * Ns;
+        }
+      } else if (Ns > 1) {  // this stage's table: span Ns, entries (r - 1) Ns + m
+        const float2* t = tab + off + m;
+#pragma unroll
+        for (int r = 1; r < P; ++r) {
+          const float2 ww = __ldg(t + (r - 1) * Ns);
+          v[r] = cmul(v[r], make_float2(ww.x, DIR > 0 ? ww.y : -ww.y));
+        }
+        off += (P - 1) * Ns;
       }
       dft_regs<P, DIR, 1, 0>(v);
       const bool last = (s == nP - 1) && rl == 0;

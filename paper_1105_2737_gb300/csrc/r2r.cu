@@ -29,6 +29,8 @@ namespace grf {
 namespace {
 
 constexpr int kR2rThreads = 512;
+constexpr bool kR2rPrefetch = false;  // twiddles loaded after each exchange: fewer spills at 64 registers
+constexpr int kR2rMinBlocks = 2;  // 64 registers: two 512-thread CTAs per SM (measured 1.4x over one)
 
 constexpr int64_t kFaceLine = int64_t(1) << 62;
 
@@ -62,8 +64,12 @@ GRF_DEV int64_t r2r_line_base(const R2rArgs& a, int64_t lg) {
   return base;
 }
 
-template <int P>
-__global__ void __launch_bounds__(kR2rThreads) r2r_line_kernel(R2rArgs a) {
+// SRC: where the lines come from (compile time, so that each kernel holds
+// only the code it runs); BC: 1 Neumann, 2 Dirichlet.
+enum R2rSrc { R2R_NOISE_ROWS = 0, R2R_LOAD_ROWS = 1, R2R_LOAD_STRIDED = 2 };
+
+template <int P, int SRC, int BC>
+__global__ void __launch_bounds__(kR2rThreads, kR2rMinBlocks) r2r_line_kernel(R2rArgs a) {
   extern __shared__ float2 sm[];
   const int C = a.C;
   const int G = 2 * C;
@@ -77,13 +83,13 @@ __global__ void __launch_bounds__(kR2rThreads) r2r_line_kernel(R2rArgs a) {
   const int64_t l0 = (int64_t)blockIdx.x * G;
   float* tile = reinterpret_cast<float*>(sm);  // [n][l]: point n of line l at n G + l
   int64_t* lbase = reinterpret_cast<int64_t*>(sm + (size_t)spad(NF) * C);
-  const bool dirichlet = a.bc == 2;
+  constexpr bool dirichlet = BC == 2;
 
   for (int l = t; l < G; l += nthr) lbase[l] = r2r_line_base(a, l0 + l);
   __syncthreads();
 
   // 1. the CTA's lines into the tile
-  if (a.noise) {  // rows of the last axis: a_K t_K, four points per Philox call
+  if constexpr (SRC == R2R_NOISE_ROWS) {  // rows of the last axis: a_K t_K, four points per Philox call
     const int NQ = (N + 3) / 4 + 1;  // calls that can touch one row of N + 1 points
     for (int u = t; u < G * NQ; u += nthr) {
       const int l = u / NQ;
@@ -108,7 +114,7 @@ __global__ void __launch_bounds__(kR2rThreads) r2r_line_kernel(R2rArgs a) {
         if (j >= j0 && j <= j0 + N) tile[(int)(j - j0) * G + l] = z[s] * __ldg(a.tab + j);
       }
     }
-  } else if (a.inner == 1) {  // contiguous rows
+  } else if constexpr (SRC == R2R_LOAD_ROWS) {  // contiguous rows
     const int W = N + 1;
     for (int e = t; e < W * G; e += nthr) {
       const int l = e / W;
@@ -141,7 +147,7 @@ __global__ void __launch_bounds__(kR2rThreads) r2r_line_kernel(R2rArgs a) {
     }
     v[q] = x;
   }
-  fft_core<P, +1>(v, sm, tau, c, C, NF, a.logNF, a.tw, a.tws, nthr);
+  fft_core<P, +1, kR2rPrefetch>(v, sm, tau, c, C, NF, a.logNF, a.tw, a.tws, nthr);
 
   // 3. outputs 0..N, separated into the two lines
   cta_sync(nthr);
@@ -159,7 +165,7 @@ __global__ void __launch_bounds__(kR2rThreads) r2r_line_kernel(R2rArgs a) {
   cta_sync(nthr);
 
   // 4. the tile back to global memory, as it was read
-  if (a.inner == 1) {
+  if constexpr (SRC != R2R_LOAD_STRIDED) {
     const int W = N + 1;
     for (int e = t; e < W * G; e += nthr) {
       const int l = e / W;
@@ -178,17 +184,27 @@ __global__ void __launch_bounds__(kR2rThreads) r2r_line_kernel(R2rArgs a) {
   }
 }
 
-template <int P>
+template <int P, int SRC, int BC>
 cudaError_t launch_r2r_t(const R2rArgs& a, cudaStream_t s) {
   const int threads = a.C * (2 * a.N / P);
   const size_t smem = r2r_smem_bytes(a.N, a.C);
   const int64_t ctas = (a.nlines + 2 * a.C - 1) / (2 * a.C);
   if (ctas > 0x7FFFFFFF) return cudaErrorInvalidValue;
-  auto k = r2r_line_kernel<P>;
+  auto k = r2r_line_kernel<P, SRC, BC>;
   cudaError_t e = prepare_kernel((const void*)k, threads, smem);
   if (e != cudaSuccess) return e;
   k<<<(unsigned)ctas, threads, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_r2r_p(int src, const R2rArgs& a, cudaStream_t s) {
+  const bool dir = a.bc == 2;
+  switch (src) {
+    case R2R_NOISE_ROWS: return dir ? launch_r2r_t<P, R2R_NOISE_ROWS, 2>(a, s) : launch_r2r_t<P, R2R_NOISE_ROWS, 1>(a, s);
+    case R2R_LOAD_ROWS: return dir ? launch_r2r_t<P, R2R_LOAD_ROWS, 2>(a, s) : launch_r2r_t<P, R2R_LOAD_ROWS, 1>(a, s);
+    default: return dir ? launch_r2r_t<P, R2R_LOAD_STRIDED, 2>(a, s) : launch_r2r_t<P, R2R_LOAD_STRIDED, 1>(a, s);
+  }
 }
 
 }  // namespace
@@ -208,10 +224,11 @@ cudaError_t launch_r2r(const R2rArgs& a, cudaStream_t s) {
   if (a.N < 2 || (a.N & (a.N - 1)) || a.N > 4096 || a.C < 1 || (a.C & (a.C - 1))) return cudaErrorInvalidValue;
   if (a.C * (2 * a.N / r2r_points_per_thread(a.N)) > kR2rThreads) return cudaErrorInvalidValue;
   if (a.noise && a.inner != 1) return cudaErrorInvalidValue;
+  const int src = a.noise ? R2R_NOISE_ROWS : (a.inner == 1 ? R2R_LOAD_ROWS : R2R_LOAD_STRIDED);
   switch (r2r_points_per_thread(a.N)) {
-    case 4: return launch_r2r_t<4>(a, s);
-    case 8: return launch_r2r_t<8>(a, s);
-    case 16: return launch_r2r_t<16>(a, s);
+    case 4: return launch_r2r_p<4>(src, a, s);
+    case 8: return launch_r2r_p<8>(src, a, s);
+    case 16: return launch_r2r_p<16>(src, a, s);
     default: return cudaErrorInvalidValue;
   }
 }
