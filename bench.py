@@ -435,6 +435,43 @@ def run_cov1d_study(args):
                               "a few times 1/sqrt(samples)"}), flush=True)
 
 
+def run_fig3_study(args):
+    """The statistical test behind the paper's Fig. 3 (§4): for the four cases
+    (m, n, k, l) of the 2-D family gamma(p) = (m^(k l) + (p_1^(2k) + p_2^(2k))^l)^(-n),
+    the covariance of grid point x_0 with every other point over 2^20 fields of
+    64^2 points on [0, 8]^2, against the exact covariance of the grid.  One JSON line."""
+    import numpy as np
+    import torch
+    from paper_1105_2737_gb300 import build
+    build()
+    from paper_1105_2737_gb300.api import GRF
+    from oracle import grf_oracle as O
+    N, Lb, count = 64, 8.0, 1 << 20
+    rows = []
+    for (m, n, k, l) in [(10.0, 1, 1, 2), (0.75, 1, 1, 2), (10.0, 3, 1, 1), (5.0, 1, 3, 1)]:
+        g = GRF((N, N), (Lb, Lb), family="paper_poly", sigma=1.0, m=m, k=k, l=l, n=n, max_batch=16384)
+        g.cov_origin(seed=0, count=16384)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sums = g.cov_origin(seed=1 << 40, count=count)
+        e1.record()
+        torch.cuda.synchronize()
+        cov = sums.cpu().numpy() / count
+        exact = O.exact_covariance((N, N), (Lb, Lb), O.Spectrum(O.PAPER_POLY, 1.0, m=m, k=k, l=l, n=n))
+        sd = np.sqrt((exact[0, 0] ** 2 + exact ** 2) / count)
+        im = np.unravel_index(np.argmin(exact), exact.shape)
+        rows.append({"m": m, "n": n, "k": k, "l": l, "c0_exact": float(exact[0, 0]), "c0_estimate": float(cov[0, 0]),
+                     "min_exact": float(exact.min()), "min_at": [int(im[0]), int(im[1])],
+                     "estimate_at_min": float(cov[im]), "max_dev_in_sd": float((np.abs(cov - exact) / sd).max()),
+                     "axis_vs_diagonal_exact": [float(exact[5, 0]), float(exact[3, 4])],
+                     "axis_vs_diagonal_estimate": [float(cov[5, 0]), float(cov[3, 4])],
+                     "ms": e0.elapsed_time(e1)})
+        g.close()
+    print(json.dumps({"study": "Fig. 3 point covariance of the 2-D polynomial family (paper §4)",
+                      "grid": [N, N], "box": [Lb, Lb], "fields": count, "rows": rows}), flush=True)
+
+
 def run_bc_study(args):
     """Neumann / Dirichlet fields (the cosine / sine transform variant): fields/s,
     Gpts/s and the HBM roofline of each pass at 2-D 4096^2 intervals (4097^2
@@ -455,6 +492,8 @@ def run_bc_study(args):
         out = torch.empty((batch,) + g.shape, dtype=torch.float32, device=dev)
         for w in range(3):
             g.sample(w * batch, batch, out)
+            if w == 0 and not rows:
+                first_field = out[0].cpu().double().numpy()  # seed 0, checked against the oracle below
         torch.cuda.synchronize()
         steps = args.steps if args.steps <= 20 else 10
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -499,11 +538,15 @@ def run_bc_study(args):
     if not args.no_cpu:
         from oracle import grf_oracle as O
         sp = O.Spectrum(family=O.MATERN, sigma=SPEC["sigma"], ell=SPEC["ell"], nu=SPEC["nu"])
+        import numpy as np
         t0 = time.perf_counter()
-        O.bc_field((4096, 4096), (1.0, 1.0), sp, O.BC_NEUMANN, 0)
+        ref = O.bc_field((4096, 4096), (1.0, 1.0), sp, O.BC_NEUMANN, 0)
         dt = time.perf_counter() - t0
         cpu = {"value": 1.0 / dt, "unit": "fields/s", "cores": torch.get_num_threads(), "kind": "oracle",
                "sample": "one 4096^2-interval Neumann field, FP64 numpy oracle, %.1f s" % dt}
+        rows[0]["error_vs_oracle_field0"] = {
+            "rel_l2": float(np.linalg.norm(first_field - ref) / np.linalg.norm(ref)),
+            "max_abs_over_sigma": float(np.abs(first_field - ref).max() / SPEC["sigma"])}
     print(json.dumps({"study": "Neumann / Dirichlet fields (cosine / sine transforms)", "rows": rows,
                       "roofline_peak_gbs": hbm, "peak_source": peak_src + " hbm_gbs (copy, burst)",
                       "cpu_baseline": cpu,
@@ -520,7 +563,7 @@ def main():
     ap.add_argument("--batch", type=int, default=BATCH, help="fields per step (profiling runs use a smaller batch)")
     ap.add_argument("--no-extras", action="store_true", help="skip the e2e, FP64 and 3-D legs")
     ap.add_argument("--no-tune", action="store_true", help="keep the default schedule (no tuning run)")
-    ap.add_argument("--study", choices=["cov1d", "bc"],
+    ap.add_argument("--study", choices=["cov1d", "bc", "fig3"],
                     help="run the paper's 1-D covariance study, or the Neumann / Dirichlet fields, instead")
     ap.add_argument("--study-samples", type=int, default=100_000_000)
     args = ap.parse_args()
@@ -528,6 +571,8 @@ def main():
         run_cov1d_study(args)
     elif args.study == "bc":
         run_bc_study(args)
+    elif args.study == "fig3":
+        run_fig3_study(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

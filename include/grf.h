@@ -305,16 +305,20 @@ grf_status grf_batch_set_debug(grf_plan p, int withhold_field, double timeout_ms
 grf_status grf_status_word(grf_plan p, void* stream);
 
 /*
- * grf_cov_origin - the Monte Carlo covariance estimator of the paper's 1-D
- * study (§4): samples the fields seed, seed + 1, ..., seed + count - 1 of a
- * 1-D FP32 plan (in chunks of max_batch, exactly as grf_sample would) and adds
- *   sums[j] += sum_b f_b(x_0) f_b(x_j),   j = 0 .. N_1 - 1,
- * where x_0 is the origin of the grid; Cov(x_j) = sums[j] / count.  FP64
- * sums, added in a fixed order (the result does not depend on scheduling).
- *   sums : device pointer, N_1 doubles, caller-owned (zero it before the
- *          first call; later calls keep adding).
+ * grf_cov_origin - the Monte Carlo covariance estimator of the paper's
+ * statistical tests (§4: the 1-D study, and the covariance of one grid point
+ * with all others behind its 2-D figures): samples the fields seed, seed + 1,
+ * ..., seed + count - 1 of an FP32 plan (periodic, or Neumann / Dirichlet; in
+ * chunks of max_batch, exactly as grf_sample would) and adds
+ *   sums[j] += sum_b f_b(x_0) f_b(x_j),   j over all points of a field (flat C order),
+ * where x_0 is the first grid point (the origin, or the corner of a boundary
+ * field); Cov(x_0, x_j) = sums[j] / count.  FP64 sums, added in a fixed order
+ * (the result does not depend on scheduling).
+ *   sums : device pointer, one double per point of a field, caller-owned (zero
+ *          it before the first call; later calls keep adding).
  * The plan keeps one chunk of fields and its partial sums (allocated on the
- * first call).  GRF_ERR_UNSUPPORTED for a plan that is not 1-D FP32.
+ * first call).  GRF_ERR_UNSUPPORTED for a batch plan, an FP64 plan, or a field
+ * of more than 2^31 - 1 points.
  */
 grf_status grf_cov_origin(grf_plan p, uint64_t seed, int64_t count, double* sums, void* stream);
 

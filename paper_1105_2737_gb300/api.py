@@ -105,11 +105,11 @@ class GRF:
         return gp
 
     def cov_origin(self, seed: int, count: int, sums: torch.Tensor | None = None) -> torch.Tensor:
-        """The estimator of the paper's 1-D study: sums[j] (+)= sum_b f_b(0) f_b(x_j)
-        over the fields seed .. seed + count - 1 (float64, on the device).
-        Cov(x_j) = sums[j] / count.  1-D FP32 plans."""
+        """The estimator of the paper's statistical tests: sums[j] (+)= sum_b f_b(0) f_b(x_j)
+        over the fields seed .. seed + count - 1 (float64, on the device, shaped like a
+        field).  Cov(x_0, x_j) = sums[j] / count.  FP32 plans."""
         if sums is None:
-            sums = torch.zeros(self.shape[0], dtype=torch.float64, device=self.device)
+            sums = torch.zeros(self.shape, dtype=torch.float64, device=self.device)
         with torch.cuda.device(self.device):
             L.grf_cov_origin(self.handle, int(seed), int(count), sums.data_ptr(), _stream_ptr(self.device))
         return sums
@@ -170,6 +170,15 @@ class GRFBoundary:
         with torch.cuda.device(self.device):
             L.grf_sample(self.handle, int(seed), int(batch), out.data_ptr(), _stream_ptr(self.device))
         return out
+
+    def cov_origin(self, seed: int, count: int, sums: torch.Tensor | None = None) -> torch.Tensor:
+        """sums[j] (+)= sum_b f_b(corner) f_b(x_j) over the fields seed .. seed + count - 1
+        (float64, shaped like a field); Cov(x_0, x_j) = sums[j] / count."""
+        if sums is None:
+            sums = torch.zeros(self.shape, dtype=torch.float64, device=self.device)
+        with torch.cuda.device(self.device):
+            L.grf_cov_origin(self.handle, int(seed), int(count), sums.data_ptr(), _stream_ptr(self.device))
+        return sums
 
     @property
     def points(self) -> int:

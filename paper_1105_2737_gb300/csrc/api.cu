@@ -1252,12 +1252,13 @@ grf_status grf_status_word(grf_plan p, void* stream) {
 grf_status grf_cov_origin(grf_plan p, uint64_t seed, int64_t count, double* sums, void* stream) {
   grf_status st = check_plan(p);
   if (st != GRF_OK) return st;
-  if (p->kind != 0 || p->d != 1 || p->prec != GRF_FP32)
-    return fail(GRF_ERR_UNSUPPORTED, "grf_cov_origin needs a 1-D FP32 plan");
+  if (p->kind == 1 || p->prec != GRF_FP32)
+    return fail(GRF_ERR_UNSUPPORTED, "grf_cov_origin needs an FP32 single-shape plan");
+  if (p->ntot > 0x7FFFFFFF) return fail(GRF_ERR_UNSUPPORTED, "grf_cov_origin: more than 2^31 - 1 points");
   if (count < 1) return fail(GRF_ERR_INVALID_ARG, "count must be >= 1");
   if (!sums) return fail(GRF_ERR_INVALID_ARG, "sums is NULL");
   cudaStream_t s = (cudaStream_t)stream;
-  const int N = (int)p->n[0];
+  const int N = (int)p->ntot;  // points per field, flat C order
   const int64_t chunk = std::min<int64_t>(p->max_batch, (int64_t)65535 * 64);
   if (!p->cov_buf) {
     GRF_CUDA(dmalloc(&p->cov_buf, (size_t)(chunk * N)), "estimator field buffer");

@@ -61,3 +61,40 @@ def test_cov_origin_within_monte_carlo_bands():
     c = O.exact_covariance((N,), (L,), SPEC)
     band = 5 * np.sqrt((c[0] ** 2 + c ** 2) / count)
     assert np.all(np.abs(cov - c) <= band), (np.abs(cov - c) / band).max()
+
+
+# the four cases of the paper's Fig. 3 (2-D polynomial family of §4),
+# gamma(p) = (m^(k l) + (p_1^(2k) + p_2^(2k))^l)^(-n), as (m, n, k, l)
+FIG3 = [(10.0, 1, 1, 2), (0.75, 1, 1, 2), (10.0, 3, 1, 1), (5.0, 1, 3, 1)]
+
+
+@pytest.mark.parametrize("m,n,k,l", FIG3)
+def test_paper_family_point_covariance(m, n, k, l):
+    """§4's statistical test of the 2-D family: the covariance of the grid point
+    x_0 with every other grid point over 2^17 fields (64^2 points on [0, 8]^2)
+    lies within 5.5 standard deviations sqrt((c(0)^2 + c(x_j)^2) / count) of the
+    exact covariance of the grid at all 4096 points, negative lobes included."""
+    from paper_1105_2737_gb300 import api
+    N, Lb, count = 64, 8.0, 1 << 17
+    g = api.GRF((N, N), (Lb, Lb), family="paper_poly", sigma=1.0, m=m, k=k, l=l, n=n, max_batch=8192)
+    cov = g.cov_origin(seed=4242, count=count).cpu().numpy() / count
+    exact = O.exact_covariance((N, N), (Lb, Lb), O.Spectrum(O.PAPER_POLY, 1.0, m=m, k=k, l=l, n=n))
+    band = 5.5 * np.sqrt((exact[0, 0] ** 2 + exact ** 2) / count)
+    assert cov.shape == (N, N)
+    assert np.all(np.abs(cov - exact) <= band), (np.abs(cov - exact) / band).max()
+    g.close()
+
+
+def test_boundary_field_corner_covariance():
+    """The estimator on a Neumann field: covariance of the corner with every
+    point over 2^17 fields against the method-of-images covariance."""
+    from paper_1105_2737_gb300 import api
+    n, Lb, count = (16, 16), (1.0, 1.0), 1 << 17
+    g = api.GRFBoundary(n, Lb, bc="neumann", family="matern", sigma=1.0, ell=0.1, nu=1.5, max_batch=8192)
+    cov = g.cov_origin(seed=99, count=count).cpu().numpy() / count
+    spec = O.Spectrum(O.MATERN, 1.0, 0.1, 1.5)
+    exact = np.array([[O.bc_exact_covariance(n, Lb, spec, O.BC_NEUMANN, (0, 0), (a, b)) for b in range(17)]
+                      for a in range(17)])
+    band = 5.5 * np.sqrt((exact[0, 0] ** 2 + exact ** 2) / count)
+    assert np.all(np.abs(cov - exact) <= band), (np.abs(cov - exact) / band).max()
+    g.close()
