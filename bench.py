@@ -472,6 +472,43 @@ def run_fig3_study(args):
                       "grid": [N, N], "box": [Lb, Lb], "fields": count, "rows": rows}), flush=True)
 
 
+def run_mixed_study(args):
+    """Sizes that are not powers of two (FP64 plain form, radix-2/3/5/7 stages):
+    fields/s at 2-D 3000^2 and 1000^2 beside the powers of two 4096^2 and 1024^2, and
+    1-D 2 * 3^7 * 5^3, with the error of one 2-D field against the FP64 oracle.
+    One JSON line."""
+    import numpy as np
+    import torch
+    from paper_1105_2737_gb300 import build
+    build()
+    from paper_1105_2737_gb300.api import GRF
+    from oracle import grf_oracle as O
+    rows = []
+    for n, batch in [((3000, 3000), 4), ((4096, 4096), 4), ((1000, 1000), 16), ((1024, 1024), 16), ((2 * 3 ** 7 * 5 ** 3,), 8)]:
+        g = GRF(n, [1.0] * len(n), precision="fp64", max_batch=batch, **SPEC)
+        out = g.sample(0, batch)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k in range(3):
+            g.sample(k * batch, batch, out)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        row = {"n": list(n), "batch": batch, "fields_per_s": batch / (ms / 1e3),
+               "gpts_per_s": batch * g.points / (ms / 1e3) / 1e9}
+        if len(n) == 2 and n[0] in (1000, 3000):  # the oracle's odd-length DFT is dense: 2-D cases only
+            f0 = out[0].cpu().numpy()
+            sp = O.Spectrum(family=O.MATERN, sigma=SPEC["sigma"], ell=SPEC["ell"], nu=SPEC["nu"])
+            ref = O.alg2_field(n, [1.0] * len(n), sp, 2 * batch)
+            row["rel_l2_vs_oracle"] = float(np.linalg.norm(f0 - ref) / np.linalg.norm(ref))
+        rows.append(row)
+        g.close()
+        del out
+        torch.cuda.empty_cache()
+    print(json.dumps({"study": "grid sizes 2^a 3^b 5^c 7^e (FP64 plain form)", "rows": rows}), flush=True)
+
+
 def run_bc_study(args):
     """Neumann / Dirichlet fields (the cosine / sine transform variant): fields/s,
     Gpts/s and the HBM roofline of each pass at 2-D 4096^2 intervals (4097^2
@@ -563,7 +600,7 @@ def main():
     ap.add_argument("--batch", type=int, default=BATCH, help="fields per step (profiling runs use a smaller batch)")
     ap.add_argument("--no-extras", action="store_true", help="skip the e2e, FP64 and 3-D legs")
     ap.add_argument("--no-tune", action="store_true", help="keep the default schedule (no tuning run)")
-    ap.add_argument("--study", choices=["cov1d", "bc", "fig3"],
+    ap.add_argument("--study", choices=["cov1d", "bc", "fig3", "mixed"],
                     help="run the paper's 1-D covariance study, or the Neumann / Dirichlet fields, instead")
     ap.add_argument("--study-samples", type=int, default=100_000_000)
     args = ap.parse_args()
@@ -573,6 +610,8 @@ def main():
         run_bc_study(args)
     elif args.study == "fig3":
         run_fig3_study(args)
+    elif args.study == "mixed":
+        run_mixed_study(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

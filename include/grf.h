@@ -59,7 +59,7 @@ extern "C" {
 typedef enum {
   GRF_OK = 0,
   GRF_ERR_INVALID_ARG = 1,   /* bad dimension, odd N_i, non-positive L_i or parameter, NULL pointer */
-  GRF_ERR_UNSUPPORTED = 2,   /* valid for the method but not built (e.g. N_i not a power of two) */
+  GRF_ERR_UNSUPPORTED = 2,   /* valid for the method but not built (e.g. N_i not a power of two in FP32) */
   GRF_ERR_OOM = 3,           /* device allocation failed */
   GRF_ERR_CUDA = 4,          /* a CUDA runtime call failed */
   GRF_ERR_TIMEOUT = 5,       /* a bounded device wait ran out (persistent batch kernel) */
@@ -105,11 +105,12 @@ typedef struct grf_plan_s* grf_plan;
  * positive gamma^(1/2), a Gaussian generator).
  *   out       : receives the plan handle (host pointer, must not be NULL).
  *   d         : dimension, 1..3.
- *   n         : host array of d grid sizes, each even, a power of two in
- *               [2, 4096] for axes 1..d-1 and in [2, 8192] for axis d of a
- *               2-D or 3-D grid; a 1-D grid goes up to 2^22 (Algorithm 2 in
- *               FP32 by a four-step c2r, and the FP64 plain form), 8192 for
- *               Algorithm 1 in FP32.
+ *   n         : host array of d grid sizes, each even, in [2, 4096] for axes
+ *               1..d-1 and in [2, 8192] for axis d of a 2-D or 3-D grid; a 1-D
+ *               grid goes up to 2^22 (Algorithm 2 in FP32 by a four-step c2r,
+ *               and the FP64 plain form), 8192 for Algorithm 1 in FP32.  FP32
+ *               plans take powers of two; FP64 plans take every even
+ *               2^a 3^b 5^c 7^e (radix-2, 3, 5 and 7 stages).
  *   L         : host array of d edge lengths, each > 0.
  *   spec      : host pointer to the spectral density parameters.
  *   alg       : grf_algorithm.

@@ -39,6 +39,12 @@ grf_status cuda_fail(cudaError_t e, const char* where) {
   } while (0)
 
 bool is_pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
+bool smooth_2357(int64_t x) {
+  if (x < 1) return false;
+  for (int p : {2, 3, 5, 7})
+    while (x % p == 0) x /= p;
+  return x == 1;
+}
 int ilog2(int64_t x) {
   int r = 0;
   while ((int64_t(1) << r) < x) ++r;
@@ -703,7 +709,11 @@ grf_status grf_plan_create(grf_plan* out, int d, const int64_t* n, const double*
     if (!(L[i] > 0) || !std::isfinite(L[i])) return fail(GRF_ERR_INVALID_ARG, "every L_i must be > 0");
   }
   for (int i = 0; i < d; ++i) {
-    if (!is_pow2(n[i])) return fail(GRF_ERR_UNSUPPORTED, "N_i must be a power of two");
+    if (prec == GRF_FP64) {  // the plain FP64 form: radix 2, 3, 5 and 7 stages
+      if (!smooth_2357(n[i])) return fail(GRF_ERR_UNSUPPORTED, "FP64: N_i must be 2^a 3^b 5^c 7^e");
+    } else if (!is_pow2(n[i])) {
+      return fail(GRF_ERR_UNSUPPORTED, "FP32: N_i must be a power of two");
+    }
     int64_t lim = (i < d - 1) ? 4096 : 8192;
     if (d == 1 && (prec == GRF_FP64 || alg == GRF_ALG_ONE_FFT)) lim = int64_t(1) << 22;  // four-step c2r
     if (n[i] > lim) return fail(GRF_ERR_UNSUPPORTED, "grid size above the supported maximum");
@@ -735,6 +745,7 @@ grf_status grf_plan_create(grf_plan* out, int d, const int64_t* n, const double*
 
   int64_t maxlen = 256;  // the length-256 table also serves Box-Muller's coarse angles
   for (int i = 0; i < d; ++i) maxlen = maxlen > n[i] ? maxlen : n[i];
+  while (!is_pow2(maxlen)) ++maxlen;  // the tables hold powers of two up to maxlen
   p->twmax = (int)maxlen;
   cudaStream_t s = nullptr;
   const SpecParams sp = spec_params(p);

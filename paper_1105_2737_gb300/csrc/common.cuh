@@ -162,7 +162,8 @@ GRF_DEV double2 alg2_xi_grid_d(int k1, int kmid, int kd, int N1, int Nmid, int M
     const double2 z = alg2_normals_grid_d(k1, kmid, kd, Nmid, M, key);
     return make_double2(z.x * r2, z.y * r2);
   }
-  const int nk1 = (N1 - k1) & (N1 - 1), nkm = (Nmid - kmid) & (Nmid - 1);
+  // -K mod N for any even N (the FP64 form also takes sizes that are not powers of two)
+  const int nk1 = k1 ? N1 - k1 : 0, nkm = kmid ? Nmid - kmid : 0;
   const int row = k1 * Nmid + kmid, nrow = nk1 * Nmid + nkm;
   if (row == nrow) return make_double2(alg2_normals_grid_d(k1, kmid, kd, Nmid, M, key).x, 0.0);
   if (row > nrow) {

@@ -44,8 +44,8 @@ __global__ void noise_full_alg2(double2* x, Full64 f, uint64_t key, int64_t tota
   bool conj_it = false;
   if (kd > f.M) {  // outside H: xi_K = conj xi_{-K}
     kd = f.n[f.d - 1] - kd;
-    k1 = (f.N1 - k1) & (f.N1 - 1);
-    km = (f.Nmid - km) & (f.Nmid - 1);
+    k1 = k1 ? f.N1 - k1 : 0;
+    km = km ? f.Nmid - km : 0;
     conj_it = true;
   }
   double2 xi = f.d == 1 ? alg2_xi_1d_d(kd, f.M, key) : alg2_xi_grid_d(k1, km, kd, f.N1, f.Nmid, f.M, key);
@@ -93,6 +93,48 @@ __global__ void stockham2_stage(const double2* __restrict__ x, double2* __restri
   y[base + (od + Ns) * inner] = csub(a, wb);
 }
 
+// One Stockham stage of radix R (2 < R <= 7, odd) along an axis of length n
+// (any n divisible by R): butterfly j < n/R reads j + q n/R (q < R), twists
+// input q by exp(dir 2 pi i m q / (R Ns)) with m = j mod Ns, takes the R-point
+// DFT and writes output q' to (j / Ns) R Ns + m + q' Ns.  After stages whose
+// radices multiply to n the result is in natural order.  Twiddles come from
+// sincospi of an exactly reduced fraction, in FP64.
+__global__ void stockham_odd_stage(const double2* __restrict__ x, double2* __restrict__ y, int n, int64_t inner,
+                                   int Ns, int R, int dir, int64_t total) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const int64_t in = t % inner;
+  const int64_t r = t / inner;
+  const int nR = n / R;
+  const int j = (int)(r % nR);
+  const int64_t o = r / nR;
+  const int64_t base = o * n * inner + in;
+  const int m = j % Ns;
+  const int64_t span = (int64_t)R * Ns;
+  double2 v[7];
+  for (int q = 0; q < R; ++q) {
+    double2 a = x[base + (int64_t)(j + q * nR) * inner];
+    if (q > 0 && m > 0) {
+      double sn, cs;
+      sincospi((double)((2 * (int64_t)m * q) % (2 * span)) / (double)span, &sn, &cs);
+      a = cmul(a, make_double2(cs, dir > 0 ? sn : -sn));
+    }
+    v[q] = a;
+  }
+  double2 root[7];  // exp(dir 2 pi i h / R), h < R
+  for (int h = 0; h < R; ++h) {
+    double sn, cs;
+    sincospi((double)(2 * h) / (double)R, &sn, &cs);
+    root[h] = make_double2(cs, dir > 0 ? sn : -sn);
+  }
+  const int64_t od = (int64_t)(j - m) * R + m;
+  for (int q2 = 0; q2 < R; ++q2) {
+    double2 acc = v[0];
+    for (int q = 1; q < R; ++q) acc = cadd(acc, cmul(v[q], root[(q * q2) % R]));
+    y[base + (od + (int64_t)q2 * Ns) * inner] = acc;
+  }
+}
+
 __global__ void real_part(const double2* x, double* out, int64_t total) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= total) return;
@@ -109,13 +151,31 @@ static cudaError_t fft_all_axes(double2** cur, double2** other, const Plain64Geo
     const int n = g.n[ax];
     int64_t inner = 1;
     for (int b = ax + 1; b < g.d; ++b) inner *= g.n[b];
-    const int64_t total = outer * (n / 2) * inner;
-    for (int Ns = 1; Ns < n; Ns *= 2) {
+    // radix-2 stages for the power-of-two factor (spans 1, 2, 4, ...: the
+    // twiddle table holds them), then one stage per odd prime factor
+    int pow2 = 1;
+    while (n % (2 * pow2) == 0) pow2 *= 2;
+    int Ns = 1;
+    for (; Ns < pow2; Ns *= 2) {
+      const int64_t total = outer * (n / 2) * inner;
       stockham2_stage<<<nblk(total, 256), 256, 0, s>>>(*cur, *other, n, inner, Ns, dir, tw, total);
       double2* t = *cur;
       *cur = *other;
       *other = t;
     }
+    int rest = n / pow2;
+    for (int R : {3, 5, 7}) {
+      while (rest % R == 0) {
+        const int64_t total = outer * (n / R) * inner;
+        stockham_odd_stage<<<nblk(total, 256), 256, 0, s>>>(*cur, *other, n, inner, Ns, R, dir, total);
+        double2* t = *cur;
+        *cur = *other;
+        *other = t;
+        Ns *= R;
+        rest /= R;
+      }
+    }
+    if (rest != 1) return cudaErrorInvalidValue;  // plan creation admits 2^a 3^b 5^c 7^e only
     outer *= n;
   }
   return cudaGetLastError();

@@ -68,6 +68,12 @@ def test_invalid_geometry(L, d, n, Ls, status):
     assert not h.value
 
 
+@pytest.mark.parametrize("n", [[22, 4], [4, 26], [2 * 3 * 11]])
+def test_fp64_rejects_prime_factors_above_7(L, n):
+    st, h = _create(L, len(n), n, [1.0] * len(n), prec=1)
+    assert st == 2 and not h.value
+
+
 def test_invalid_parameters(L):
     for kw in [dict(sigma=0.0), dict(ell=-1.0), dict(nu=0.0), dict(family=7)]:
         st, _ = _create(L, 2, [8, 8], [1.0, 1.0], spec=L.make_spectrum(**kw))

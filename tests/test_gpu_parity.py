@@ -141,6 +141,33 @@ def test_fp64_plain_form(n, alg):
     assert e <= 1e-12, e
 
 
+# sizes whose odd part is 3, 5 or 7 (the FP64 plain form's radix-3/5/7 stages);
+# Lb anisotropic, Gaussian and paper families too
+MIXED = [((6,), "matern"), ((10,), "gaussian"), ((14,), "matern"), ((30,), "paper_poly"), ((1000,), "matern"),
+         ((12, 20), "matern"), ((96, 80), "gaussian"), ((6, 10, 14), "matern"), ((2, 42, 6), "paper_poly"),
+         ((3000,), "matern")]
+
+
+@pytest.mark.parametrize("case", range(len(MIXED)))
+@pytest.mark.parametrize("alg", [2, 1])
+def test_fp64_mixed_radix_sizes(case, alg):
+    n, fam = MIXED[case]
+    kw = dict(ell=0.1, nu=1.5) if fam != "paper_poly" else dict(m=2.0, k=1, l=2, n=1)
+    Lb = tuple(1.0 + 0.25 * i for i in range(len(n)))
+    g = _api().GRF(n, Lb, family=fam, alg=alg, precision="fp64", max_batch=2, **kw)
+    f = g.sample(seed=3, batch=2).cpu().numpy()
+    ref = O.sample(n, Lb, _ospec(fam, **kw), seed=3, batch=2, alg=alg)
+    e = np.linalg.norm(f - ref) / np.linalg.norm(ref)
+    assert e <= 1e-12, e
+    assert np.abs(f - ref).max() <= 1e-12 * np.abs(ref).max() * 10
+
+
+def test_fp32_rejects_mixed_radix_sizes():
+    from paper_1105_2737_gb300 import _lib as L
+    with pytest.raises(L.GRFError):
+        _api().GRF((12, 16), (1.0, 1.0), precision="fp32")
+
+
 def test_same_seed_same_fields_and_batch_split():
     g = _api().GRF((128, 64), (1.0, 1.0), ell=0.05, nu=1.5, max_batch=8)
     a = g.sample(seed=100, batch=8).clone()

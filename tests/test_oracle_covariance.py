@@ -40,7 +40,8 @@ def _alg1_linear_map(n, L, spec):
 
 
 @pytest.mark.parametrize("n,L", [((8,), (1.0,)), ((8, 8), (1.0, 1.0)), ((4, 6), (0.7, 1.9)),
-                                 ((4, 4, 4), (1.0, 1.0, 1.0)), ((2, 4, 6), (1.0, 2.0, 0.5)), ((2,), (1.0,))])
+                                 ((4, 4, 4), (1.0, 1.0, 1.0)), ((2, 4, 6), (1.0, 2.0, 0.5)), ((2,), (1.0,)),
+                                 ((10,), (1.3,)), ((14,), (2.0,)), ((6, 10), (1.0, 0.8))])
 @pytest.mark.parametrize("si", range(len(SPECS)))
 def test_linear_map_covariance_is_circulant(n, L, si):
     spec = SPECS[si]
