@@ -59,7 +59,7 @@ extern "C" {
 typedef enum {
   GRF_OK = 0,
   GRF_ERR_INVALID_ARG = 1,   /* bad dimension, odd N_i, non-positive L_i or parameter, NULL pointer */
-  GRF_ERR_UNSUPPORTED = 2,   /* valid for the method but not built (e.g. N_i not a power of two in FP32) */
+  GRF_ERR_UNSUPPORTED = 2,   /* valid for the method but not built (e.g. a prime factor of N_i above 7) */
   GRF_ERR_OOM = 3,           /* device allocation failed */
   GRF_ERR_CUDA = 4,          /* a CUDA runtime call failed */
   GRF_ERR_TIMEOUT = 5,       /* a bounded device wait ran out (persistent batch kernel) */
@@ -108,9 +108,12 @@ typedef struct grf_plan_s* grf_plan;
  *   n         : host array of d grid sizes, each even, in [2, 4096] for axes
  *               1..d-1 and in [2, 8192] for axis d of a 2-D or 3-D grid; a 1-D
  *               grid goes up to 2^22 (Algorithm 2 in FP32 by a four-step c2r,
- *               and the FP64 plain form), 8192 for Algorithm 1 in FP32.  FP32
- *               plans take powers of two; FP64 plans take every even
- *               2^a 3^b 5^c 7^e (radix-2, 3, 5 and 7 stages).
+ *               and the FP64 plain form), 8192 for Algorithm 1 in FP32.  Every
+ *               even 2^a 3^b 5^c 7^e is taken: FP32 plans on powers of two run
+ *               the fused kernels; FP64 plans, and FP32 plans with another size
+ *               on some axis, run the plain form (one launch sequence per
+ *               field, radix-2, 3, 5 and 7 Stockham stages; such FP32 plans have
+ *               no adjoint, rfft or tuner).
  *   L         : host array of d edge lengths, each > 0.
  *   spec      : host pointer to the spectral density parameters.
  *   alg       : grf_algorithm.
@@ -350,7 +353,7 @@ enum {
   GRF_KERNEL_ROWS_C2R = 2,      /* c2r along the last axis */
   GRF_KERNEL_ROWS_R2C = 3,      /* r2c along the last axis */
   GRF_KERNEL_ROWS_1D = 4,       /* 1-D single-pass kernels */
-  GRF_KERNEL_PLAIN64 = 5,       /* one field of the plain FP64 form (a launch sequence) */
+  GRF_KERNEL_PLAIN64 = 5,       /* one field of the plain form (a launch sequence; FP64, or FP32 off powers of two) */
   GRF_KERNEL_REDUCE = 6,        /* adjoint final sum */
   GRF_KERNEL_R2R_NOISE = 7,     /* boundary fields: noise + cosine / sine transform along the last axis */
   GRF_KERNEL_R2R = 8            /* boundary fields: cosine / sine transform along a strided axis */

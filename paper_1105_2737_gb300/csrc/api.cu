@@ -174,6 +174,14 @@ struct grf_plan_s {
   double* stab64 = nullptr;
   double2* bufA = nullptr;
   double2* bufB = nullptr;
+  // FP32 plans on grids that are not powers of two take the plain form in FP32
+  bool mixed = false;
+  float2* buf32A = nullptr;
+  float2* buf32B = nullptr;
+  // per-axis twiddles exp(2 pi i k / N_i) of the plain form's radix-3/5/7 stages
+  // (axes whose size is not a power of two; NULL otherwise)
+  double2* twax64[3] = {nullptr, nullptr, nullptr};
+  float2* twax32[3] = {nullptr, nullptr, nullptr};
 
   // host delivery
   static constexpr int kCopyStreams = 4;
@@ -219,6 +227,12 @@ void free_plan(grf_plan p) {
   cudaFree(p->stab64);
   cudaFree(p->bufA);
   cudaFree(p->bufB);
+  cudaFree(p->buf32A);
+  cudaFree(p->buf32B);
+  for (int i = 0; i < 3; ++i) {
+    cudaFree(p->twax64[i]);
+    cudaFree(p->twax32[i]);
+  }
   for (int i = 0; i < 2; ++i) {
     cudaFree(p->stage[i]);
     if (p->ev_done[i]) cudaEventDestroy(p->ev_done[i]);
@@ -708,14 +722,17 @@ grf_status grf_plan_create(grf_plan* out, int d, const int64_t* n, const double*
     if (n[i] < 2 || (n[i] & 1)) return fail(GRF_ERR_INVALID_ARG, "every N_i must be even and >= 2");
     if (!(L[i] > 0) || !std::isfinite(L[i])) return fail(GRF_ERR_INVALID_ARG, "every L_i must be > 0");
   }
+  // powers of two take the fused FP32 kernels; other sizes 2^a 3^b 5^c 7^e the
+  // plain form (radix 2, 3, 5 and 7 stages), in FP64 or FP32
+  bool all_pow2 = true;
   for (int i = 0; i < d; ++i) {
-    if (prec == GRF_FP64) {  // the plain FP64 form: radix 2, 3, 5 and 7 stages
-      if (!smooth_2357(n[i])) return fail(GRF_ERR_UNSUPPORTED, "FP64: N_i must be 2^a 3^b 5^c 7^e");
-    } else if (!is_pow2(n[i])) {
-      return fail(GRF_ERR_UNSUPPORTED, "FP32: N_i must be a power of two");
-    }
+    if (!smooth_2357(n[i])) return fail(GRF_ERR_UNSUPPORTED, "N_i must be 2^a 3^b 5^c 7^e");
+    all_pow2 = all_pow2 && is_pow2(n[i]);
+  }
+  const bool mixed = prec == GRF_FP32 && !all_pow2;
+  for (int i = 0; i < d; ++i) {
     int64_t lim = (i < d - 1) ? 4096 : 8192;
-    if (d == 1 && (prec == GRF_FP64 || alg == GRF_ALG_ONE_FFT)) lim = int64_t(1) << 22;  // four-step c2r
+    if (d == 1 && (prec == GRF_FP64 || alg == GRF_ALG_ONE_FFT || mixed)) lim = int64_t(1) << 22;  // four-step c2r
     if (n[i] > lim) return fail(GRF_ERR_UNSUPPORTED, "grid size above the supported maximum");
   }
 
@@ -730,6 +747,7 @@ grf_status grf_plan_create(grf_plan* out, int d, const int64_t* n, const double*
   p->alg = alg;
   p->prec = prec;
   p->max_batch = max_batch;
+  p->mixed = mixed;
   cudaGetDevice(&p->device);
   p->M = (int)(n[d - 1] / 2);
   p->N1 = d >= 2 ? (int)n[0] : 1;
@@ -762,7 +780,20 @@ grf_status grf_plan_create(grf_plan* out, int d, const int64_t* n, const double*
 
   PLAN_CUDA(dmalloc(&p->status, 1), "status word");
   PLAN_CUDA(cudaMemset(p->status, 0, sizeof(int)), "status word");
-  if (prec == GRF_FP32) {
+  if (mixed) {
+    PLAN_CUDA(dmalloc(&p->tw, 2 * maxlen + kStageTableEntries), "twiddle table");
+    PLAN_CUDA(build_twiddles(p->tw, (int)maxlen, s), "twiddle build");
+    PLAN_CUDA(dmalloc(&p->stab, p->fold_size), "s table");
+    PLAN_CUDA(build_stab(p->stab, nullptr, sp, 0.0, s), "s table build");
+    PLAN_CUDA(dmalloc(&p->buf32A, p->ntot), "FP32 plain buffer");
+    PLAN_CUDA(dmalloc(&p->buf32B, p->ntot), "FP32 plain buffer");
+    for (int i = 0; i < d; ++i)
+      if (!is_pow2(n[i])) {
+        PLAN_CUDA(dmalloc(&p->twax32[i], n[i]), "axis twiddles");
+        PLAN_CUDA(build_axis_twiddles(p->twax32[i], (int)n[i], s), "axis twiddles");
+      }
+    p->chunk = max_batch;
+  } else if (prec == GRF_FP32) {
     PLAN_CUDA(dmalloc(&p->tw, 2 * maxlen + kStageTableEntries), "twiddle table");
     PLAN_CUDA(build_twiddles(p->tw, (int)maxlen, s), "twiddle build");
     PLAN_CUDA(dmalloc(&p->stab, p->fold_size), "s table");
@@ -812,6 +843,11 @@ grf_status grf_plan_create(grf_plan* out, int d, const int64_t* n, const double*
     PLAN_CUDA(build_stab_d(p->stab64, sp, s), "FP64 s table build");
     PLAN_CUDA(dmalloc(&p->bufA, p->ntot), "FP64 buffer");
     PLAN_CUDA(dmalloc(&p->bufB, p->ntot), "FP64 buffer");
+    for (int i = 0; i < d; ++i)
+      if (!is_pow2(n[i])) {
+        PLAN_CUDA(dmalloc(&p->twax64[i], n[i]), "axis twiddles");
+        PLAN_CUDA(build_axis_twiddles(p->twax64[i], (int)n[i], s), "axis twiddles");
+      }
   }
   PLAN_CUDA(cudaStreamSynchronize(s), "plan table build");
 #undef PLAN_CUDA
@@ -851,15 +887,21 @@ grf_status grf_sample(grf_plan p, uint64_t seed, int64_t batch, void* out, void*
   if (!out) return fail(GRF_ERR_INVALID_ARG, "out is NULL");
   if (batch < 1 || batch > p->max_batch) return fail(GRF_ERR_INVALID_ARG, "batch must be in [1, max_batch]");
   cudaStream_t s = (cudaStream_t)stream;
-  if (p->prec == GRF_FP64) {
+  if (p->prec == GRF_FP64 || p->mixed) {
     Plain64Geom g{};
     g.d = p->d;
     for (int i = 0; i < 3; ++i) g.n[i] = (int)p->n[i];
     for (int64_t b = 0; b < batch; ++b) {
-      TLAUNCH(GRF_KERNEL_PLAIN64,
-              plain64_field(g, p->alg, seed + (uint64_t)b, p->stab64, p->tw64, p->bufA, p->bufB,
-                            (double*)out + b * p->ntot, s),
-              "FP64 plain field");
+      if (p->mixed)
+        TLAUNCH(GRF_KERNEL_PLAIN64,
+                plain32_field(g, p->alg, seed + (uint64_t)b, p->stab, p->tw, p->twax32, p->tw + 256, p->buf32A,
+                              p->buf32B, (float*)out + b * p->ntot, s),
+                "FP32 plain field");
+      else
+        TLAUNCH(GRF_KERNEL_PLAIN64,
+                plain64_field(g, p->alg, seed + (uint64_t)b, p->stab64, p->tw64, p->twax64, p->bufA, p->bufB,
+                              (double*)out + b * p->ntot, s),
+                "FP64 plain field");
     }
     return GRF_OK;
   }
@@ -897,8 +939,8 @@ grf_status grf_sample(grf_plan p, uint64_t seed, int64_t batch, void* out, void*
 grf_status grf_plan_tune(grf_plan p, void* stream) {
   grf_status st = check_plan(p);
   if (st != GRF_OK) return st;
-  if (p->kind != 0 || p->prec != GRF_FP32 || p->d < 2)
-    return fail(GRF_ERR_UNSUPPORTED, "the tuner covers FP32 2-D and 3-D plans");
+  if (p->kind != 0 || p->prec != GRF_FP32 || p->d < 2 || p->mixed)
+    return fail(GRF_ERR_UNSUPPORTED, "the tuner covers FP32 2-D and 3-D plans on powers of two");
   const char* force = std::getenv("GRF_TUNE_FORCE");
   if (p->sched_cached && !(force && force[0] == '1')) return GRF_OK;  // already tuned on this GPU
   cudaStream_t s = (cudaStream_t)stream;
@@ -1093,9 +1135,12 @@ grf_status grf_sample_host(grf_plan p, uint64_t seed, int64_t batch, void* host_
       g.d = p->d;
       for (int i = 0; i < 3; ++i) g.n[i] = (int)p->n[i];
       for (int64_t b = 0; b < nb; ++b)
-        LAUNCH(plain64_field(g, p->alg, seed + (uint64_t)(f0 + b), p->stab64, p->tw64, p->bufA, p->bufB,
+        LAUNCH(plain64_field(g, p->alg, seed + (uint64_t)(f0 + b), p->stab64, p->tw64, p->twax64, p->bufA, p->bufB,
                              (double*)p->stage[slot] + b * p->ntot, s),
                "FP64 plain field");
+    } else if (p->mixed) {
+      st = grf_sample(p, seed + (uint64_t)f0, nb, p->stage[slot], stream);
+      if (st != GRF_OK) return st;
     } else {
       st = sample_chunk_fp32(p, seed, f0, nb, (float*)p->stage[slot], s);
       if (st != GRF_OK) return st;
@@ -1127,8 +1172,8 @@ grf_status grf_backward(grf_plan p, uint64_t seed, int64_t batch, const void* gr
   if (p->kind != 0) return fail(GRF_ERR_INVALID_ARG, "batch plans have no adjoint");
   if (!grad_out || !grad_params) return fail(GRF_ERR_INVALID_ARG, "NULL pointer");
   if (batch < 1 || batch > p->max_batch) return fail(GRF_ERR_INVALID_ARG, "batch must be in [1, max_batch]");
-  if (p->prec != GRF_FP32 || p->alg != GRF_ALG_ONE_FFT)
-    return fail(GRF_ERR_UNSUPPORTED, "the adjoint is built for FP32 Algorithm 2 plans");
+  if (p->prec != GRF_FP32 || p->alg != GRF_ALG_ONE_FFT || p->mixed)
+    return fail(GRF_ERR_UNSUPPORTED, "the adjoint is built for FP32 Algorithm 2 plans on powers of two");
   if (!p->dstab) return fail(GRF_ERR_UNSUPPORTED, "the adjoint needs a Matern or Gaussian spectrum without normalize_discrete");
   if (p->d == 1 && p->M > 4096) return fail(GRF_ERR_UNSUPPORTED, "the adjoint is built for 1-D grids up to 8192");
   cudaStream_t s = (cudaStream_t)stream;
@@ -1171,7 +1216,7 @@ grf_status grf_rfft_forward(grf_plan p, int64_t batch, const void* in, void* out
   if (p->kind != 0) return fail(GRF_ERR_INVALID_ARG, "batch plans have no rfft");
   if (!in || !out_halfspec) return fail(GRF_ERR_INVALID_ARG, "NULL pointer");
   if (batch < 1 || batch > p->max_batch) return fail(GRF_ERR_INVALID_ARG, "batch must be in [1, max_batch]");
-  if (p->prec != GRF_FP32) return fail(GRF_ERR_UNSUPPORTED, "rfft is built for FP32 plans");
+  if (p->prec != GRF_FP32 || p->mixed) return fail(GRF_ERR_UNSUPPORTED, "rfft is built for FP32 plans on powers of two");
   if (p->d == 1 && p->M > 4096) return fail(GRF_ERR_UNSUPPORTED, "rfft is built for 1-D grids up to 8192");
   cudaStream_t s = (cudaStream_t)stream;
   const HalfGeom g = half_geom(p, 0, 0);

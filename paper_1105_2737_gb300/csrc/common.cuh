@@ -146,7 +146,7 @@ GRF_DEV float2 alg2_xi_grid(int k1, int kmid, int kd, int N1, int Nmid, int M, u
     const float2 z = alg2_normals_grid(k1, kmid, kd, Nmid, M, key, trig);
     return make_float2(z.x * r2, z.y * r2);
   }
-  const int nk1 = (N1 - k1) & (N1 - 1), nkm = (Nmid - kmid) & (Nmid - 1);
+  const int nk1 = k1 ? N1 - k1 : 0, nkm = kmid ? Nmid - kmid : 0;  // -K mod N for any even N
   const int row = k1 * Nmid + kmid, nrow = nk1 * Nmid + nkm;
   if (row == nrow) return make_float2(alg2_normals_grid(k1, kmid, kd, Nmid, M, key, trig).x, 0.0f);
   if (row > nrow) {

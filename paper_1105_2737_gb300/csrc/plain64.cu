@@ -1,14 +1,30 @@
-// Plain FP64 form of the method: one field per launch sequence, nothing fused.
+// Plain form of the method: one field per launch sequence, nothing fused.
 //   noise kernel (xi on the full grid, Hermitian by Eq. conj, or real z for
 //   Algorithm 1) -> HBM; scale kernel (s_K, or s_K / sqrt(N_tot) after the
-//   forward transform of Algorithm 1); radix-2 Stockham FFT, one launch per
-//   stage, along every axis over the full complex grid; real part.
-// It is the FP64 comparator of the fused FP32 path and the GRF_FP64 plans.
+//   forward transform of Algorithm 1); Stockham FFT (radix 2, then 3, 5, 7),
+//   one launch per stage, along every axis over the full complex grid; real part.
+// In FP64 it is the comparator of the fused FP32 path and the GRF_FP64 plans;
+// in FP32 it serves FP32 plans on grids that are not powers of two (the fused
+// kernels take powers of two), with the noise of the fused path.
+#include <type_traits>
 #include "kernels.h"
 #include "common.cuh"
 #include "plain64.h"
 
 namespace grf {
+
+template <class R>
+struct cplx;
+template <>
+struct cplx<float> {
+  using t = float2;
+  static __device__ t make(double re, double im) { return make_float2((float)re, (float)im); }
+};
+template <>
+struct cplx<double> {
+  using t = double2;
+  static __device__ t make(double re, double im) { return make_double2(re, im); }
+};
 
 struct Full64 {
   int d;
@@ -36,7 +52,8 @@ __device__ void split_full(int64_t idx, const Full64& f, int* k1, int* km, int* 
   }
 }
 
-__global__ void noise_full_alg2(double2* x, Full64 f, uint64_t key, int64_t total) {
+template <class R>
+__global__ void noise_full_alg2(typename cplx<R>::t* x, Full64 f, uint64_t key, int64_t total, const float2* trig) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= total) return;
   int k1, km, kd;
@@ -48,32 +65,43 @@ __global__ void noise_full_alg2(double2* x, Full64 f, uint64_t key, int64_t tota
     km = km ? f.Nmid - km : 0;
     conj_it = true;
   }
-  double2 xi = f.d == 1 ? alg2_xi_1d_d(kd, f.M, key) : alg2_xi_grid_d(k1, km, kd, f.N1, f.Nmid, f.M, key);
+  typename cplx<R>::t xi;
+  if constexpr (std::is_same<R, double>::value)
+    xi = f.d == 1 ? alg2_xi_1d_d(kd, f.M, key) : alg2_xi_grid_d(k1, km, kd, f.N1, f.Nmid, f.M, key);
+  else
+    xi = f.d == 1 ? alg2_xi_1d(kd, f.M, key, trig) : alg2_xi_grid(k1, km, kd, f.N1, f.Nmid, f.M, key, trig);
   if (conj_it) xi.y = -xi.y;
   x[i] = xi;
 }
 
-__global__ void noise_full_alg1(double2* x, uint64_t key, int64_t total) {
+template <class R>
+__global__ void noise_full_alg1(typename cplx<R>::t* x, uint64_t key, int64_t total, const float2* trig) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= total) return;
-  x[i] = make_double2(alg1_normal_d((uint64_t)i, key), 0.0);
+  if constexpr (std::is_same<R, double>::value)
+    x[i] = make_double2(alg1_normal_d((uint64_t)i, key), 0.0);
+  else
+    x[i] = make_float2(alg1_normal((uint64_t)i, key, trig), 0.0f);
 }
 
-// x_K *= factor * s_K, s from the FP64 folded table.
-__global__ void scale_full(double2* x, const double* stab, Full64 f, double factor, int64_t total) {
+// x_K *= factor * s_K, s from the folded table.
+template <class R>
+__global__ void scale_full(typename cplx<R>::t* x, const R* stab, Full64 f, R factor, int64_t total) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= total) return;
   int k1, km, kd;
   split_full(i, f, &k1, &km, &kd);
   const int f1 = min(k1, f.N1 - k1), fm = min(km, f.Nmid - km), fd = min(kd, f.n[f.d - 1] - kd);
-  const double s = stab[((int64_t)fd * (f.Nmid / 2 + 1) + fm) * (f.N1 / 2 + 1) + f1];
+  const R s = stab[((int64_t)fd * (f.Nmid / 2 + 1) + fm) * (f.N1 / 2 + 1) + f1];
   x[i] = cscale(x[i], s * factor);
 }
 
 // One radix-2 Stockham stage along an axis of length n viewed as [outer][n][inner]:
 // butterfly j < n/2 reads j, j + n/2 and writes (j / Ns) 2 Ns + j % Ns (+ Ns).
-__global__ void stockham2_stage(const double2* __restrict__ x, double2* __restrict__ y, int n, int64_t inner,
-                                int Ns, int dir, const double2* __restrict__ tw, int64_t total) {
+template <class R>
+__global__ void stockham2_stage(const typename cplx<R>::t* __restrict__ x, typename cplx<R>::t* __restrict__ y, int n,
+                                int64_t inner, int Ns, int dir, const typename cplx<R>::t* __restrict__ tw,
+                                int64_t total) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= total) return;
   const int64_t in = t % inner;
@@ -82,12 +110,12 @@ __global__ void stockham2_stage(const double2* __restrict__ x, double2* __restri
   const int j = (int)(r % half);
   const int64_t o = r / half;
   const int64_t base = o * n * inner + in;
-  const double2 a = x[base + (int64_t)j * inner];
-  const double2 b = x[base + (int64_t)(j + half) * inner];
+  const auto a = x[base + (int64_t)j * inner];
+  const auto b = x[base + (int64_t)(j + half) * inner];
   const int m = j & (Ns - 1);
-  double2 w = tw[2 * Ns + m];  // exp(2 pi i m / (2 Ns))
+  auto w = tw[2 * Ns + m];  // exp(2 pi i m / (2 Ns))
   if (dir < 0) w.y = -w.y;
-  const double2 wb = cmul(w, b);
+  const auto wb = cmul(w, b);
   const int64_t od = (int64_t)((j - m) * 2 + m);
   y[base + od * inner] = cadd(a, wb);
   y[base + (od + Ns) * inner] = csub(a, wb);
@@ -97,10 +125,15 @@ __global__ void stockham2_stage(const double2* __restrict__ x, double2* __restri
 // (any n divisible by R): butterfly j < n/R reads j + q n/R (q < R), twists
 // input q by exp(dir 2 pi i m q / (R Ns)) with m = j mod Ns, takes the R-point
 // DFT and writes output q' to (j / Ns) R Ns + m + q' Ns.  After stages whose
-// radices multiply to n the result is in natural order.  Twiddles come from
-// sincospi of an exactly reduced fraction, in FP64.
-__global__ void stockham_odd_stage(const double2* __restrict__ x, double2* __restrict__ y, int n, int64_t inner,
-                                   int Ns, int R, int dir, int64_t total) {
+// radices multiply to n the result is in natural order.  Every twiddle is an
+// entry of the axis table twn[k] = exp(2 pi i k / n) (R Ns divides n):
+// exp(2 pi i m q / (R Ns)) = twn[m q n / (R Ns)] (m q < R Ns), and the DFT's
+// roots exp(2 pi i h / R) = twn[h n / R].
+template <class T>
+__global__ void stockham_odd_stage(const typename cplx<T>::t* __restrict__ x, typename cplx<T>::t* __restrict__ y,
+                                   int n, int64_t inner, int Ns, int R, int dir, const typename cplx<T>::t* __restrict__ twn,
+                                   int64_t total) {
+  using C = cplx<T>;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= total) return;
   const int64_t in = t % inner;
@@ -110,32 +143,32 @@ __global__ void stockham_odd_stage(const double2* __restrict__ x, double2* __res
   const int64_t o = r / nR;
   const int64_t base = o * n * inner + in;
   const int m = j % Ns;
-  const int64_t span = (int64_t)R * Ns;
-  double2 v[7];
+  const int step = n / (R * Ns);  // twn index of exp(2 pi i / (R Ns))
+  typename C::t v[7];
   for (int q = 0; q < R; ++q) {
-    double2 a = x[base + (int64_t)(j + q * nR) * inner];
+    typename C::t a = x[base + (int64_t)(j + q * nR) * inner];
     if (q > 0 && m > 0) {
-      double sn, cs;
-      sincospi((double)((2 * (int64_t)m * q) % (2 * span)) / (double)span, &sn, &cs);
-      a = cmul(a, make_double2(cs, dir > 0 ? sn : -sn));
+      typename C::t w = twn[m * q * step];
+      if (dir < 0) w.y = -w.y;
+      a = cmul(a, w);
     }
     v[q] = a;
   }
-  double2 root[7];  // exp(dir 2 pi i h / R), h < R
+  typename C::t root[7];  // exp(dir 2 pi i h / R), h < R
   for (int h = 0; h < R; ++h) {
-    double sn, cs;
-    sincospi((double)(2 * h) / (double)R, &sn, &cs);
-    root[h] = make_double2(cs, dir > 0 ? sn : -sn);
+    root[h] = twn[h * nR];
+    if (dir < 0) root[h].y = -root[h].y;
   }
   const int64_t od = (int64_t)(j - m) * R + m;
   for (int q2 = 0; q2 < R; ++q2) {
-    double2 acc = v[0];
+    typename C::t acc = v[0];
     for (int q = 1; q < R; ++q) acc = cadd(acc, cmul(v[q], root[(q * q2) % R]));
     y[base + (od + (int64_t)q2 * Ns) * inner] = acc;
   }
 }
 
-__global__ void real_part(const double2* x, double* out, int64_t total) {
+template <class R>
+__global__ void real_part(const typename cplx<R>::t* x, R* out, int64_t total) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= total) return;
   out[i] = x[i].x;
@@ -144,8 +177,9 @@ __global__ void real_part(const double2* x, double* out, int64_t total) {
 static inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 // Full complex DFT along every axis; result ends in *cur (ping-pong with *other).
-static cudaError_t fft_all_axes(double2** cur, double2** other, const Plain64Geom& g, int dir,
-                                const double2* tw, cudaStream_t s) {
+template <class R>
+static cudaError_t fft_all_axes(typename cplx<R>::t** cur, typename cplx<R>::t** other, const Plain64Geom& g, int dir,
+                                const typename cplx<R>::t* tw, const typename cplx<R>::t* const* twax, cudaStream_t s) {
   int64_t outer = 1;
   for (int ax = 0; ax < g.d; ++ax) {
     const int n = g.n[ax];
@@ -158,21 +192,22 @@ static cudaError_t fft_all_axes(double2** cur, double2** other, const Plain64Geo
     int Ns = 1;
     for (; Ns < pow2; Ns *= 2) {
       const int64_t total = outer * (n / 2) * inner;
-      stockham2_stage<<<nblk(total, 256), 256, 0, s>>>(*cur, *other, n, inner, Ns, dir, tw, total);
-      double2* t = *cur;
+      stockham2_stage<R><<<nblk(total, 256), 256, 0, s>>>(*cur, *other, n, inner, Ns, dir, tw, total);
+      auto t = *cur;
       *cur = *other;
       *other = t;
     }
     int rest = n / pow2;
-    for (int R : {3, 5, 7}) {
-      while (rest % R == 0) {
-        const int64_t total = outer * (n / R) * inner;
-        stockham_odd_stage<<<nblk(total, 256), 256, 0, s>>>(*cur, *other, n, inner, Ns, R, dir, total);
-        double2* t = *cur;
+    for (int Rd : {3, 5, 7}) {
+      while (rest % Rd == 0) {
+        const int64_t total = outer * (n / Rd) * inner;
+        if (!twax || !twax[ax]) return cudaErrorInvalidValue;
+        stockham_odd_stage<R><<<nblk(total, 256), 256, 0, s>>>(*cur, *other, n, inner, Ns, Rd, dir, twax[ax], total);
+        auto t = *cur;
         *cur = *other;
         *other = t;
-        Ns *= R;
-        rest /= R;
+        Ns *= Rd;
+        rest /= Rd;
       }
     }
     if (rest != 1) return cudaErrorInvalidValue;  // plan creation admits 2^a 3^b 5^c 7^e only
@@ -181,8 +216,11 @@ static cudaError_t fft_all_axes(double2** cur, double2** other, const Plain64Geo
   return cudaGetLastError();
 }
 
-cudaError_t plain64_field(const Plain64Geom& g, int alg, uint64_t key, const double* stab, const double2* tw,
-                          double2* bufA, double2* bufB, double* out, cudaStream_t s) {
+template <class R>
+static cudaError_t plain_field(const Plain64Geom& g, int alg, uint64_t key, const R* stab,
+                               const typename cplx<R>::t* tw, const typename cplx<R>::t* const* twax,
+                               const float2* trig, typename cplx<R>::t* bufA, typename cplx<R>::t* bufB, R* out,
+                               cudaStream_t s) {
   Full64 f{};
   f.d = g.d;
   for (int i = 0; i < 3; ++i) f.n[i] = i < g.d ? g.n[i] : 1;
@@ -192,20 +230,50 @@ cudaError_t plain64_field(const Plain64Geom& g, int alg, uint64_t key, const dou
   f.Nmid = g.d == 3 ? g.n[1] : 1;
   int64_t total = 1;
   for (int i = 0; i < g.d; ++i) total *= g.n[i];
-  double2* cur = bufA;
-  double2* other = bufB;
+  auto cur = bufA;
+  auto other = bufB;
   if (alg == 2) {
-    noise_full_alg2<<<nblk(total, 256), 256, 0, s>>>(cur, f, key, total);
-    scale_full<<<nblk(total, 256), 256, 0, s>>>(cur, stab, f, 1.0, total);
+    noise_full_alg2<R><<<nblk(total, 256), 256, 0, s>>>(cur, f, key, total, trig);
+    scale_full<R><<<nblk(total, 256), 256, 0, s>>>(cur, stab, f, (R)1, total);
   } else {
-    noise_full_alg1<<<nblk(total, 256), 256, 0, s>>>(cur, key, total);
-    cudaError_t e = fft_all_axes(&cur, &other, g, -1, tw, s);
+    noise_full_alg1<R><<<nblk(total, 256), 256, 0, s>>>(cur, key, total, trig);
+    cudaError_t e = fft_all_axes<R>(&cur, &other, g, -1, tw, twax, s);
     if (e != cudaSuccess) return e;
-    scale_full<<<nblk(total, 256), 256, 0, s>>>(cur, stab, f, 1.0 / sqrt((double)total), total);
+    scale_full<R><<<nblk(total, 256), 256, 0, s>>>(cur, stab, f, (R)(1.0 / sqrt((double)total)), total);
   }
-  cudaError_t e = fft_all_axes(&cur, &other, g, +1, tw, s);
+  cudaError_t e = fft_all_axes<R>(&cur, &other, g, +1, tw, twax, s);
   if (e != cudaSuccess) return e;
-  real_part<<<nblk(total, 256), 256, 0, s>>>(cur, out, total);
+  real_part<R><<<nblk(total, 256), 256, 0, s>>>(cur, out, total);
+  return cudaGetLastError();
+}
+
+cudaError_t plain64_field(const Plain64Geom& g, int alg, uint64_t key, const double* stab, const double2* tw,
+                          const double2* const* twax, double2* bufA, double2* bufB, double* out, cudaStream_t s) {
+  return plain_field<double>(g, alg, key, stab, tw, twax, nullptr, bufA, bufB, out, s);
+}
+
+cudaError_t plain32_field(const Plain64Geom& g, int alg, uint64_t key, const float* stab, const float2* tw,
+                          const float2* const* twax, const float2* trig, float2* bufA, float2* bufB, float* out,
+                          cudaStream_t s) {
+  return plain_field<float>(g, alg, key, stab, tw, twax, trig, bufA, bufB, out, s);
+}
+
+// twn[k] = exp(2 pi i k / n), k < n, from sincospi of the exact fraction 2k/n in FP64.
+template <class R>
+__global__ void axis_twiddle_kernel(typename cplx<R>::t* twn, int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  double sn, cs;
+  sincospi(2.0 * (double)k / (double)n, &sn, &cs);
+  twn[k] = cplx<R>::make(cs, sn);
+}
+
+cudaError_t build_axis_twiddles(double2* twn, int n, cudaStream_t s) {
+  axis_twiddle_kernel<double><<<nblk(n, 256), 256, 0, s>>>(twn, n);
+  return cudaGetLastError();
+}
+cudaError_t build_axis_twiddles(float2* twn, int n, cudaStream_t s) {
+  axis_twiddle_kernel<float><<<nblk(n, 256), 256, 0, s>>>(twn, n);
   return cudaGetLastError();
 }
 

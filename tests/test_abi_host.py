@@ -58,7 +58,7 @@ def _create(L, d, n, Ls, spec=None, alg=2, prec=0, max_batch=1):
     (2, [5, 4], [1.0, 1.0], 1),    # odd N
     (2, [4, 0], [1.0, 1.0], 1),
     (2, [4, 4], [1.0, -1.0], 1),   # non-positive L
-    (2, [6, 4], [1.0, 1.0], 2),    # even but not a power of two
+    (2, [22, 4], [1.0, 1.0], 2),   # even, with a prime factor above 7
     (2, [8192, 4], [1.0, 1.0], 2), # axis 1 above 4096
     (1, [2 ** 23], [1.0], 2),
 ])

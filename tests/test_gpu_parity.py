@@ -162,10 +162,26 @@ def test_fp64_mixed_radix_sizes(case, alg):
     assert np.abs(f - ref).max() <= 1e-12 * np.abs(ref).max() * 10
 
 
-def test_fp32_rejects_mixed_radix_sizes():
+@pytest.mark.parametrize("case", range(len(MIXED)))
+@pytest.mark.parametrize("alg", [2, 1])
+def test_fp32_mixed_radix_sizes(case, alg):
+    """FP32 plans off powers of two (the FP32 plain form) within the FP32 bar."""
+    n, fam = MIXED[case]
+    kw = dict(ell=0.1, nu=1.5) if fam != "paper_poly" else dict(m=2.0, k=1, l=2, n=1)
+    Lb = tuple(1.0 + 0.25 * i for i in range(len(n)))
+    g = _api().GRF(n, Lb, family=fam, alg=alg, precision="fp32", max_batch=2, **kw)
+    f = g.sample(seed=3, batch=2).cpu().numpy()
+    ref = O.sample(n, Lb, _ospec(fam, **kw), seed=3, batch=2, alg=alg)
+    _compare(f, ref, sigma=1.0 if fam != "paper_poly" else float(np.sqrt((ref ** 2).mean())))
+
+
+def test_fp32_mixed_plan_has_no_adjoint_or_rfft():
     from paper_1105_2737_gb300 import _lib as L
+    g = _api().GRF((12, 20), (1.0, 1.0), precision="fp32", max_batch=1)
     with pytest.raises(L.GRFError):
-        _api().GRF((12, 16), (1.0, 1.0), precision="fp32")
+        g.backward(0, torch.zeros((1, 12, 20), device="cuda"))
+    with pytest.raises(L.GRFError):
+        g.rfft(torch.zeros((1, 12, 20), device="cuda"))
 
 
 def test_same_seed_same_fields_and_batch_split():
