@@ -527,6 +527,8 @@ def run_bc_study(args):
     dev = torch.device("cuda", 0)
     rows = []
     cases = [((4096, 4096), 16, "neumann"), ((4096, 4096), 16, "dirichlet"), ((256, 256, 256), 4, "neumann")]
+    if args.batch != BATCH:  # a smaller case (profiling): the 2-D Neumann grid with --batch fields
+        cases = [((4096, 4096), args.batch, "neumann")]
     for n, batch, bc in cases:
         g = GRFBoundary(n, [1.0] * len(n), bc=bc, max_batch=batch, **SPEC)
         out = torch.empty((batch,) + g.shape, dtype=torch.float32, device=dev)
