@@ -264,7 +264,7 @@ def test_invalid_calls_raise():
     with pytest.raises(GRFError):
         g.sample(seed=0, batch=3)
     with pytest.raises(GRFError):
-        api.GRF((24, 32), (1.0, 1.0))
+        api.GRF((22, 32), (1.0, 1.0))  # prime factor 11
     g64 = api.GRF((32, 32), (1.0, 1.0), precision="fp64")
     with pytest.raises(GRFError):
         g64.backward(0, torch.zeros((1, 32, 32), dtype=torch.float64, device="cuda"))
