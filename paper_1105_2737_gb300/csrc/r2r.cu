@@ -81,7 +81,10 @@ __global__ void __launch_bounds__(kR2rThreads, kR2rMinBlocks) r2r_line_kernel(R2
   const int c = t & (C - 1);
   const int tau = t >> a.logC;
   const int64_t l0 = (int64_t)blockIdx.x * G;
-  float* tile = reinterpret_cast<float*>(sm);  // [n][l]: point n of line l at n G + l
+  // the tile of the CTA's lines: rows (contiguous lines) line-major, point n of
+  // line l at l W + n; strided lines point-major, at n G + l (G = 2C lines)
+  float* tile = reinterpret_cast<float*>(sm);
+  const int W = N + 1;
   int64_t* lbase = reinterpret_cast<int64_t*>(sm + (size_t)spad(NF) * C);
   constexpr bool dirichlet = BC == 2;
 
@@ -96,7 +99,7 @@ __global__ void __launch_bounds__(kR2rThreads, kR2rMinBlocks) r2r_line_kernel(R2
       const int qi = u - l * NQ;
       const int64_t base = lbase[l];
       if (base < 0 || base >= kFaceLine) {
-        for (int n = qi; n <= N; n += NQ) tile[n * G + l] = 0.f;
+        for (int n = qi; n <= N; n += NQ) tile[l * W + n] = 0.f;
         continue;
       }
       const int64_t b = (l0 + l) / a.lines_per_field;
@@ -111,24 +114,34 @@ __global__ void __launch_bounds__(kR2rThreads, kR2rMinBlocks) r2r_line_kernel(R2
 #pragma unroll
       for (int s = 0; s < 4; ++s) {
         const int64_t j = 4 * m + s;
-        if (j >= j0 && j <= j0 + N) tile[(int)(j - j0) * G + l] = z[s] * __ldg(a.tab + j);
+        if (j >= j0 && j <= j0 + N) tile[l * W + (int)(j - j0)] = z[s] * __ldg(a.tab + j);
       }
     }
   } else if constexpr (SRC == R2R_LOAD_ROWS) {  // contiguous rows
-    const int W = N + 1;
     for (int e = t; e < W * G; e += nthr) {
       const int l = e / W;
       const int n = e - l * W;
       const int64_t base = lbase[l];
-      tile[n * G + l] = (base >= 0 && base < kFaceLine) ? __ldcg(a.f + base + n) : 0.f;
+      tile[e] = (base >= 0 && base < kFaceLine) ? __ldcg(a.f + base + n) : 0.f;
     }
-  } else {  // strided axis: neighbouring lines are neighbours in memory
-    const int E = (N + 1) * G;
-    for (int e = t; e < E; e += nthr) {
-      const int n = e >> a.logG;
-      const int l = e & (G - 1);
-      const int64_t base = lbase[l];
-      tile[e] = (base >= 0 && base < kFaceLine) ? __ldcg(a.f + base + (int64_t)n * a.inner) : 0.f;
+  } else {  // strided axis: neighbouring lines are neighbours in memory;
+            // eight loads in flight per thread before they go to the tile
+    const int E = W * G;
+    constexpr int U = 8;
+    for (int e0 = t; e0 < E; e0 += U * nthr) {
+      float x[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * nthr;
+        x[u] = 0.f;
+        if (e < E) {
+          const int64_t base = lbase[e & (G - 1)];
+          if (base >= 0 && base < kFaceLine) x[u] = __ldcg(a.f + base + (int64_t)(e >> a.logG) * a.inner);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (e0 + u * nthr < E) tile[e0 + u * nthr] = x[u];
     }
   }
   cta_sync(nthr);
@@ -140,7 +153,9 @@ __global__ void __launch_bounds__(kR2rThreads, kR2rMinBlocks) r2r_line_kernel(R2
   for (int q = 0; q < P; ++q) {
     const int n = tau + TPT * q;
     const int nn = n <= N ? n : NF - n;
-    float2 x = tile2[nn * C + c];
+    float2 x;
+    if constexpr (SRC == R2R_LOAD_STRIDED) x = tile2[nn * C + c];
+    else x = make_float2(tile[2 * c * W + nn], tile[(2 * c + 1) * W + nn]);
     if (dirichlet) {
       if (n == 0 || n == N) x = make_float2(0.f, 0.f);
       else if (n > N) x = make_float2(-x.x, -x.y);
@@ -159,22 +174,26 @@ __global__ void __launch_bounds__(kR2rThreads, kR2rMinBlocks) r2r_line_kernel(R2
       const float2 y = v[q];
       float2 o = y;
       if (dirichlet) o = (k == 0 || k == N) ? make_float2(0.f, 0.f) : make_float2(y.y, -y.x);
-      out2[k * C + c] = o;
+      if constexpr (SRC == R2R_LOAD_STRIDED) {
+        out2[k * C + c] = o;
+      } else {
+        tile[2 * c * W + k] = o.x;
+        tile[(2 * c + 1) * W + k] = o.y;
+      }
     }
   }
   cta_sync(nthr);
 
   // 4. the tile back to global memory, as it was read
   if constexpr (SRC != R2R_LOAD_STRIDED) {
-    const int W = N + 1;
     for (int e = t; e < W * G; e += nthr) {
       const int l = e / W;
       const int n = e - l * W;
       const int64_t base = lbase[l];
-      if (base >= 0) a.f[(base & (kFaceLine - 1)) + n] = base < kFaceLine ? tile[n * G + l] : 0.f;
+      if (base >= 0) a.f[(base & (kFaceLine - 1)) + n] = base < kFaceLine ? tile[e] : 0.f;
     }
   } else {
-    const int E = (N + 1) * G;
+    const int E = W * G;
     for (int e = t; e < E; e += nthr) {
       const int n = e >> a.logG;
       const int l = e & (G - 1);
