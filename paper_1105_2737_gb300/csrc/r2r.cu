@@ -86,9 +86,21 @@ __global__ void __launch_bounds__(kR2rThreads, kR2rMinBlocks) r2r_line_kernel(R2
   float* tile = reinterpret_cast<float*>(sm);
   const int W = N + 1;
   int64_t* lbase = reinterpret_cast<int64_t*>(sm + (size_t)spad(NF) * C);
+  int64_t* lj0 = lbase + G;  // noise launch: flat index of point 0 of each line in its field
+  uint64_t* lkey = reinterpret_cast<uint64_t*>(lj0 + G);  // and the Philox key of its field
   constexpr bool dirichlet = BC == 2;
 
-  for (int l = t; l < G; l += nthr) lbase[l] = r2r_line_base(a, l0 + l);
+  for (int l = t; l < G; l += nthr) {
+    const int64_t base = r2r_line_base(a, l0 + l);
+    lbase[l] = base;
+    if constexpr (SRC == R2R_NOISE_ROWS) {
+      if (base >= 0) {
+        const int64_t b = (l0 + l) / a.lines_per_field;
+        lj0[l] = (base & (kFaceLine - 1)) - b * a.field_stride;
+        lkey[l] = a.seed + (uint64_t)(a.field0 + b);
+      }
+    }
+  }
   __syncthreads();
 
   // 1. the CTA's lines into the tile
@@ -102,12 +114,10 @@ __global__ void __launch_bounds__(kR2rThreads, kR2rMinBlocks) r2r_line_kernel(R2
         for (int n = qi; n <= N; n += NQ) tile[l * W + n] = 0.f;
         continue;
       }
-      const int64_t b = (l0 + l) / a.lines_per_field;
-      const int64_t j0 = base - b * a.field_stride;  // flat index of point 0 in its field
+      const int64_t j0 = lj0[l];
       const int64_t m = (j0 >> 2) + qi;
       if (4 * m > j0 + N) continue;
-      const uint64_t key = a.seed + (uint64_t)(a.field0 + b);
-      const u32x4 w = philox_call((uint64_t)m, 2u, key);
+      const u32x4 w = philox_call((uint64_t)m, 2u, lkey[l]);
       const float2 z01 = box_muller(w.x, w.y, a.trig);
       const float2 z23 = box_muller(w.z, w.w, a.trig);
       const float z[4] = {z01.x, z01.y, z23.x, z23.y};
@@ -228,7 +238,9 @@ cudaError_t launch_r2r_p(int src, const R2rArgs& a, cudaStream_t s) {
 
 }  // namespace
 
-size_t r2r_smem_bytes(int N, int C) { return (size_t)spad_h(2 * N) * C * sizeof(float2) + 2 * C * sizeof(int64_t); }
+// FFT scratch (which also holds the tile), then per line: the offset of point
+// 0, and for the noise launch its flat index in the field and its Philox key
+size_t r2r_smem_bytes(int N, int C) { return (size_t)spad_h(2 * N) * C * sizeof(float2) + 3 * 2 * C * sizeof(int64_t); }
 
 int r2r_points_per_thread(int N) { return 2 * N >= 16 ? 16 : 2 * N; }
 
