@@ -41,7 +41,8 @@ def _sources():
 def _fingerprint() -> str:
     h = hashlib.sha256()
     h.update(platform.machine().encode())
-    h.update(" ".join(ARCH + NVCC_FLAGS).encode())
+    # the flags without the -I paths: the value must not depend on where the tree sits
+    h.update(" ".join(ARCH + [f for f in NVCC_FLAGS if not f.startswith("-I")]).encode())
     for d in (CSRC, INCLUDE):
         for f in sorted(os.listdir(d)):
             if f.endswith((".cu", ".cuh", ".h", ".cpp")):
