@@ -355,6 +355,34 @@ def run_ours(args):
     ub.close()
     del uouts
 
+    # Neumann fields of 4097^2 points (cosine transforms), batch 16, and a grid
+    # that is not a power of two (3000^2, FP32 plain form), batch 4
+    from paper_1105_2737_gb300.api import GRFBoundary
+
+    def _time_calls(fn, k):
+        fn(0)
+        torch.cuda.synchronize()
+        d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        d0.record(stream)
+        for i in range(k):
+            fn(i + 1)
+        d1.record(stream)
+        torch.cuda.synchronize()
+        return d0.elapsed_time(d1) / k
+
+    gb = GRFBoundary(SHAPE, (1.0, 1.0), bc="neumann", max_batch=16, **SPEC)
+    ob = torch.empty((16,) + gb.shape, dtype=torch.float32, device="cuda")
+    ms_b = _time_calls(lambda i: gb.sample(i * 16, 16, ob), 5)
+    pts_b = gb.points
+    gb.close()
+    del ob
+    gm = GRF((3000, 3000), (1.0, 1.0), max_batch=4, **SPEC)
+    om = gm.empty(4)
+    ms_m = _time_calls(lambda i: gm.sample(i * 4, 4, om), 3)
+    gm.close()
+    del om
+    torch.cuda.empty_cache()
+
     if rank != 0:
         return
     cpu_val, cpu_s, cores = _oracle_fields_per_s(1) if not args.no_cpu else (None, None, None)
@@ -376,6 +404,10 @@ def run_ours(args):
         "extra_uneven_batch_4096": {"fields_per_s": 4096 / (ms_u / 1000.0), "gpts_per_s": upoints / (ms_u / 1e3) / 1e9,
                                     "ms_per_launch": ms_u, "points": upoints, "status": ustatus,
                                     "launch": "one persistent kernel per batch, CUDA graph replay"},
+        "extra_neumann_4097sq_batch16": {"fields_per_s": 16 / (ms_b / 1000.0), "gpts_per_s": 16 * pts_b / (ms_b / 1e3) / 1e9,
+                                         "ms_per_call": ms_b, "launches_per_call": 2},
+        "extra_3000sq_fp32_plain_batch4": {"fields_per_s": 4 / (ms_m / 1000.0), "gpts_per_s": 4 * 9e6 / (ms_m / 1e3) / 1e9,
+                                           "ms_per_call": ms_m},
         "e2e": {"value": e2e_val, "unit": "fields/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": BATCH * ntot * 4,
                 "variants_fields_per_s": e2e_var,
