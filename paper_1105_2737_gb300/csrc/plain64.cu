@@ -98,25 +98,26 @@ __global__ void scale_full(typename cplx<R>::t* x, const R* stab, Full64 f, R fa
 
 // One radix-2 Stockham stage along an axis of length n viewed as [outer][n][inner]:
 // butterfly j < n/2 reads j, j + n/2 and writes (j / Ns) 2 Ns + j % Ns (+ Ns).
-template <class R>
+// IX: the index type, 32-bit when the grid has fewer than 2^31 points (the
+// divisions below are then 32-bit), else 64-bit.
+template <class R, class IX>
 __global__ void stockham2_stage(const typename cplx<R>::t* __restrict__ x, typename cplx<R>::t* __restrict__ y, int n,
-                                int64_t inner, int Ns, int dir, const typename cplx<R>::t* __restrict__ tw,
-                                int64_t total) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                                IX inner, int Ns, int dir, const typename cplx<R>::t* __restrict__ tw, IX total) {
+  const IX t = (IX)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= total) return;
-  const int64_t in = t % inner;
-  const int64_t r = t / inner;
+  const IX in = t % inner;
+  const IX r = t / inner;
   const int half = n >> 1;
   const int j = (int)(r % half);
-  const int64_t o = r / half;
-  const int64_t base = o * n * inner + in;
-  const auto a = x[base + (int64_t)j * inner];
-  const auto b = x[base + (int64_t)(j + half) * inner];
+  const IX o = r / half;
+  const IX base = o * n * inner + in;
+  const auto a = x[base + (IX)j * inner];
+  const auto b = x[base + (IX)(j + half) * inner];
   const int m = j & (Ns - 1);
   auto w = tw[2 * Ns + m];  // exp(2 pi i m / (2 Ns))
   if (dir < 0) w.y = -w.y;
   const auto wb = cmul(w, b);
-  const int64_t od = (int64_t)((j - m) * 2 + m);
+  const IX od = (IX)((j - m) * 2 + m);
   y[base + od * inner] = cadd(a, wb);
   y[base + (od + Ns) * inner] = csub(a, wb);
 }
@@ -129,24 +130,25 @@ __global__ void stockham2_stage(const typename cplx<R>::t* __restrict__ x, typen
 // entry of the axis table twn[k] = exp(2 pi i k / n) (R Ns divides n):
 // exp(2 pi i m q / (R Ns)) = twn[m q n / (R Ns)] (m q < R Ns), and the DFT's
 // roots exp(2 pi i h / R) = twn[h n / R].
-template <class T>
+template <class T, int R, class IX>
 __global__ void stockham_odd_stage(const typename cplx<T>::t* __restrict__ x, typename cplx<T>::t* __restrict__ y,
-                                   int n, int64_t inner, int Ns, int R, int dir, const typename cplx<T>::t* __restrict__ twn,
-                                   int64_t total) {
+                                   int n, IX inner, int Ns, int dir, const typename cplx<T>::t* __restrict__ twn,
+                                   IX total) {
   using C = cplx<T>;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const IX t = (IX)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= total) return;
-  const int64_t in = t % inner;
-  const int64_t r = t / inner;
+  const IX in = t % inner;
+  const IX r = t / inner;
   const int nR = n / R;
   const int j = (int)(r % nR);
-  const int64_t o = r / nR;
-  const int64_t base = o * n * inner + in;
+  const IX o = r / nR;
+  const IX base = o * n * inner + in;
   const int m = j % Ns;
   const int step = n / (R * Ns);  // twn index of exp(2 pi i / (R Ns))
-  typename C::t v[7];
+  typename C::t v[R];
+#pragma unroll
   for (int q = 0; q < R; ++q) {
-    typename C::t a = x[base + (int64_t)(j + q * nR) * inner];
+    typename C::t a = x[base + (IX)(j + q * nR) * inner];
     if (q > 0 && m > 0) {
       typename C::t w = twn[m * q * step];
       if (dir < 0) w.y = -w.y;
@@ -154,17 +156,29 @@ __global__ void stockham_odd_stage(const typename cplx<T>::t* __restrict__ x, ty
     }
     v[q] = a;
   }
-  typename C::t root[7];  // exp(dir 2 pi i h / R), h < R
+  typename C::t root[R];  // exp(dir 2 pi i h / R), h < R
+#pragma unroll
   for (int h = 0; h < R; ++h) {
     root[h] = twn[h * nR];
     if (dir < 0) root[h].y = -root[h].y;
   }
-  const int64_t od = (int64_t)(j - m) * R + m;
+  const IX od = (IX)(j - m) * R + m;
+#pragma unroll
   for (int q2 = 0; q2 < R; ++q2) {
     typename C::t acc = v[0];
+#pragma unroll
     for (int q = 1; q < R; ++q) acc = cadd(acc, cmul(v[q], root[(q * q2) % R]));
-    y[base + (od + (int64_t)q2 * Ns) * inner] = acc;
+    y[base + (od + (IX)q2 * Ns) * inner] = acc;
   }
+}
+
+template <class T, class IX>
+static void launch_odd_stage(int R, const typename cplx<T>::t* x, typename cplx<T>::t* y, int n, IX inner, int Ns,
+                             int dir, const typename cplx<T>::t* twn, IX total, cudaStream_t s) {
+  const unsigned blocks = (unsigned)((total + 255) / 256);
+  if (R == 3) stockham_odd_stage<T, 3, IX><<<blocks, 256, 0, s>>>(x, y, n, inner, Ns, dir, twn, total);
+  else if (R == 5) stockham_odd_stage<T, 5, IX><<<blocks, 256, 0, s>>>(x, y, n, inner, Ns, dir, twn, total);
+  else stockham_odd_stage<T, 7, IX><<<blocks, 256, 0, s>>>(x, y, n, inner, Ns, dir, twn, total);
 }
 
 template <class R>
@@ -190,9 +204,13 @@ static cudaError_t fft_all_axes(typename cplx<R>::t** cur, typename cplx<R>::t**
     int pow2 = 1;
     while (n % (2 * pow2) == 0) pow2 *= 2;
     int Ns = 1;
+    const bool small = outer * n * inner < ((int64_t)1 << 31);  // 32-bit indices
     for (; Ns < pow2; Ns *= 2) {
       const int64_t total = outer * (n / 2) * inner;
-      stockham2_stage<R><<<nblk(total, 256), 256, 0, s>>>(*cur, *other, n, inner, Ns, dir, tw, total);
+      if (small)
+        stockham2_stage<R, int><<<nblk(total, 256), 256, 0, s>>>(*cur, *other, n, (int)inner, Ns, dir, tw, (int)total);
+      else
+        stockham2_stage<R, int64_t><<<nblk(total, 256), 256, 0, s>>>(*cur, *other, n, inner, Ns, dir, tw, total);
       auto t = *cur;
       *cur = *other;
       *other = t;
@@ -202,7 +220,10 @@ static cudaError_t fft_all_axes(typename cplx<R>::t** cur, typename cplx<R>::t**
       while (rest % Rd == 0) {
         const int64_t total = outer * (n / Rd) * inner;
         if (!twax || !twax[ax]) return cudaErrorInvalidValue;
-        stockham_odd_stage<R><<<nblk(total, 256), 256, 0, s>>>(*cur, *other, n, inner, Ns, Rd, dir, twax[ax], total);
+        if (small)
+          launch_odd_stage<R, int>(Rd, *cur, *other, n, (int)inner, Ns, dir, twax[ax], (int)total, s);
+        else
+          launch_odd_stage<R, int64_t>(Rd, *cur, *other, n, inner, Ns, dir, twax[ax], total, s);
         auto t = *cur;
         *cur = *other;
         *other = t;
