@@ -152,11 +152,14 @@ grf_status grf_plan_create(grf_plan* out, int d, const int64_t* n, const double*
  *   L    : host array of d edge lengths, each > 0.
  *   spec : any family; normalize_discrete must be 0 (else GRF_ERR_UNSUPPORTED).
  *   bc   : grf_boundary.
- * grf_sample on the plan writes batch * prod (N_i + 1) floats; grf_plan_query
- * answers keys 0 (points per field), 3..6 and 16 (bc); grf_plan_timing
- * records its launches (GRF_KERNEL_R2R_NOISE, GRF_KERNEL_R2R).  The other
- * calls return GRF_ERR_INVALID_ARG for such a plan.  The plan holds the
- * FP64-computed, FP32-rounded c_K (prod (N_i + 1) floats) and the twiddles.
+ * grf_sample on the plan writes batch * prod (N_i + 1) floats, grf_sample_host
+ * the same fields to host memory; grf_plan_set_spectrum rebuilds c_K;
+ * grf_cov_origin estimates the covariance of the corner with every point;
+ * grf_plan_query answers keys 0 (points per field), 3..6 and 16 (bc);
+ * grf_plan_timing records its launches (GRF_KERNEL_R2R_NOISE, GRF_KERNEL_R2R).
+ * grf_backward, grf_rfft_forward and grf_plan_tune return an error for such
+ * a plan.  The plan holds the FP64-computed, FP32-rounded c_K
+ * (prod (N_i + 1) floats) and the twiddles.
  */
 grf_status grf_bc_plan_create(grf_plan* out, int d, const int64_t* n, const double* L,
                               const grf_spectrum* spec, int bc, int64_t max_batch);

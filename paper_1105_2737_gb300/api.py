@@ -171,6 +171,22 @@ class GRFBoundary:
             L.grf_sample(self.handle, int(seed), int(batch), out.data_ptr(), _stream_ptr(self.device))
         return out
 
+    def sample_host(self, seed: int = 0, batch: int = 1, out: torch.Tensor | None = None) -> torch.Tensor:
+        """The same fields delivered to (pinned) host memory."""
+        if out is None:
+            out = torch.empty((batch,) + self.shape, dtype=torch.float32, pin_memory=True)
+        assert out.is_contiguous() and out.dtype == torch.float32 and out.device.type == "cpu"
+        with torch.cuda.device(self.device):
+            L.grf_sample_host(self.handle, int(seed), int(batch), out.data_ptr(), _stream_ptr(self.device))
+        return out
+
+    def set_params(self, family: str, sigma: float = 1.0, ell: float = 0.1, nu: float = 1.5, m: float = 1.0,
+                   k: int = 1, l: int = 1, n: int = 1):
+        """New spectral parameters of the same family: rebuilds c_K on the current stream."""
+        spec = L.make_spectrum(_FAMILIES[family], sigma, ell, nu, m, k, l, n, 0)
+        with torch.cuda.device(self.device):
+            L.grf_plan_set_spectrum(self.handle, spec, _stream_ptr(self.device))
+
     def cov_origin(self, seed: int, count: int, sums: torch.Tensor | None = None) -> torch.Tensor:
         """sums[j] (+)= sum_b f_b(corner) f_b(x_j) over the fields seed .. seed + count - 1
         (float64, shaped like a field); Cov(x_0, x_j) = sums[j] / count."""

@@ -671,6 +671,7 @@ grf_status grf_bc_plan_create(grf_plan* out, int d, const int64_t* n, const doub
   p->max_batch = max_batch;
   p->bc = bc;
   p->ntot = ntot;
+  p->chunk = max_batch;  // host delivery: fields per staged chunk at most
   cudaGetDevice(&p->device);
   int64_t maxlen = 256;  // the length-256 table also serves Box-Muller's coarse angles
   for (int i = 0; i < d; ++i) maxlen = std::max<int64_t>(maxlen, 2 * n[i]);
@@ -860,12 +861,17 @@ grf_status grf_plan_create(grf_plan* out, int d, const int64_t* n, const double*
 grf_status grf_plan_set_spectrum(grf_plan p, const grf_spectrum* spec, void* stream) {
   grf_status st = check_plan(p);
   if (st != GRF_OK) return st;
-  if (p->kind != 0) return fail(GRF_ERR_INVALID_ARG, "batch plans keep their spectra");
+  if (p->kind == 1) return fail(GRF_ERR_INVALID_ARG, "batch plans keep their spectra");
   st = validate_spec(spec);
   if (st != GRF_OK) return st;
   if (spec->family != p->spec.family || (spec->normalize_discrete != 0) != (p->spec.normalize_discrete != 0))
     return fail(GRF_ERR_INVALID_ARG, "the family and normalisation mode are fixed at plan creation");
   cudaStream_t s = (cudaStream_t)stream;
+  if (p->kind == 2) {  // boundary fields: the c_K table
+    p->spec = *spec;
+    LAUNCH(build_bc_table(p->bctab, spec_params(p), p->bc, s), "boundary c_K table build");
+    return GRF_OK;
+  }
   p->spec = *spec;
   p->norm_scale = spec->normalize_discrete ? spec->sigma * spec->sigma / discrete_sum(p) : 1.0;
   const SpecParams sp = spec_params(p);
@@ -1077,7 +1083,7 @@ grf_status grf_plan_tune(grf_plan p, void* stream) {
 grf_status grf_sample_host(grf_plan p, uint64_t seed, int64_t batch, void* host_out, void* stream) {
   grf_status st = check_plan(p);
   if (st != GRF_OK) return st;
-  if (p->kind != 0) return fail(GRF_ERR_INVALID_ARG, "batch plans use grf_batch_sample");
+  if (p->kind == 1) return fail(GRF_ERR_INVALID_ARG, "batch plans use grf_batch_sample");
   if (!host_out) return fail(GRF_ERR_INVALID_ARG, "host_out is NULL");
   if (batch < 1 || batch > p->max_batch) return fail(GRF_ERR_INVALID_ARG, "batch must be in [1, max_batch]");
   cudaStream_t s = (cudaStream_t)stream;
@@ -1138,7 +1144,7 @@ grf_status grf_sample_host(grf_plan p, uint64_t seed, int64_t batch, void* host_
         LAUNCH(plain64_field(g, p->alg, seed + (uint64_t)(f0 + b), p->stab64, p->tw64, p->twax64, p->bufA, p->bufB,
                              (double*)p->stage[slot] + b * p->ntot, s),
                "FP64 plain field");
-    } else if (p->mixed) {
+    } else if (p->mixed || p->kind == 2) {
       st = grf_sample(p, seed + (uint64_t)f0, nb, p->stage[slot], stream);
       if (st != GRF_OK) return st;
     } else {
@@ -1169,7 +1175,7 @@ grf_status grf_backward(grf_plan p, uint64_t seed, int64_t batch, const void* gr
                         void* stream) {
   grf_status st = check_plan(p);
   if (st != GRF_OK) return st;
-  if (p->kind != 0) return fail(GRF_ERR_INVALID_ARG, "batch plans have no adjoint");
+  if (p->kind != 0) return fail(GRF_ERR_INVALID_ARG, "the adjoint is built for periodic single-shape plans");
   if (!grad_out || !grad_params) return fail(GRF_ERR_INVALID_ARG, "NULL pointer");
   if (batch < 1 || batch > p->max_batch) return fail(GRF_ERR_INVALID_ARG, "batch must be in [1, max_batch]");
   if (p->prec != GRF_FP32 || p->alg != GRF_ALG_ONE_FFT || p->mixed)
@@ -1213,7 +1219,7 @@ grf_status grf_backward(grf_plan p, uint64_t seed, int64_t batch, const void* gr
 grf_status grf_rfft_forward(grf_plan p, int64_t batch, const void* in, void* out_halfspec, void* stream) {
   grf_status st = check_plan(p);
   if (st != GRF_OK) return st;
-  if (p->kind != 0) return fail(GRF_ERR_INVALID_ARG, "batch plans have no rfft");
+  if (p->kind != 0) return fail(GRF_ERR_INVALID_ARG, "rfft is built for periodic single-shape plans");
   if (!in || !out_halfspec) return fail(GRF_ERR_INVALID_ARG, "NULL pointer");
   if (batch < 1 || batch > p->max_batch) return fail(GRF_ERR_INVALID_ARG, "batch must be in [1, max_batch]");
   if (p->prec != GRF_FP32 || p->mixed) return fail(GRF_ERR_UNSUPPORTED, "rfft is built for FP32 plans on powers of two");

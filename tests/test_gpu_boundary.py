@@ -127,3 +127,26 @@ def test_boundary_variance_is_image_sum(bc):
     band = 6 * np.sqrt(2.0 / count) * want + 1e-12
     assert np.all(np.abs(var - want) <= band), np.max(np.abs(var - want) / band)
     g.close()
+
+
+def test_boundary_set_spectrum_and_host_delivery():
+    """grf_plan_set_spectrum rebuilds c_K (fields equal a fresh plan's, bit for
+    bit); grf_sample_host delivers the same fields as grf_sample."""
+    api = _api()
+    n, L = (64, 32), (1.0, 0.5)
+    g = api.GRFBoundary(n, L, bc="dirichlet", family="matern", ell=0.1, nu=1.5, max_batch=3)
+    g.set_params("matern", sigma=1.3, ell=0.05, nu=2.5)
+    a = g.sample(11, 3)
+    fresh = api.GRFBoundary(n, L, bc="dirichlet", family="matern", sigma=1.3, ell=0.05, nu=2.5, max_batch=3)
+    b = fresh.sample(11, 3)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    h = g.sample_host(11, 3)
+    assert torch.equal(h, a.cpu())
+    ref = O.bc_field(n, L, _ospec("matern", sigma=1.3, ell=0.05, nu=2.5), O.BC_DIRICHLET, 12)
+    _compare(h[1].numpy(), ref, sigma=1.3)
+    from paper_1105_2737_gb300 import _lib as Lb
+    with pytest.raises(Lb.GRFError):
+        g.set_params("gaussian", ell=0.1)  # the family is fixed at creation
+    g.close()
+    fresh.close()
