@@ -29,6 +29,7 @@ SHAPE = (4096, 4096)
 BATCH = 64
 SPEC = dict(family="matern", sigma=1.0, ell=0.05, nu=2.5)
 WORKLOAD = "2-D 4096x4096 FP32 Matern(sigma=1, ell=0.05, nu=2.5) on [0,1]^2, Algorithm 2, batch 64, seeds step*64+b"
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e nominal bandwidth (context beside the measured copy figure)
 PAPER_FIELDS_PER_S = 4.0  # 0.25 s for one 512x512 field on the paper's machine (context only)
 
 
@@ -397,6 +398,10 @@ def run_ours(args):
         "roofline": roofline,
         "roofline_c2r": hbm_roofline("rows_c2r") if "rows_c2r" in per_kind else None,
         "per_pass_hbm_frac": per_pass_frac, "strict_hbm_frac": strict_frac, "passes_P": P,
+        "nominal_hbm": {"gbs": NOMINAL_HBM_GBS, "per_pass_frac": per_pass_frac * peak / NOMINAL_HBM_GBS,
+                        "strict_frac": strict_frac * peak / NOMINAL_HBM_GBS,
+                        "c2r_frac": (hbm_roofline("rows_c2r")["achieved"] / NOMINAL_HBM_GBS
+                                     if "rows_c2r" in per_kind else None)},
         "passes": passes,
         "fp64_plain": {"fields_per_s": fp64_fields_per_s, "ratio_fp32_batched_over_fp64_plain": value / ws / fp64_fields_per_s},
         "extra_3d_256cubed_batch8": {"fields_per_s": fields3, "gpts_per_s": fields3 * 256 ** 3 / 1e9,
