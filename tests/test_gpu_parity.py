@@ -175,6 +175,17 @@ def test_fp32_mixed_radix_sizes(case, alg):
     _compare(f, ref, sigma=1.0 if fam != "paper_poly" else float(np.sqrt((ref ** 2).mean())))
 
 
+def test_fp32_mixed_radix_full_size_3000sq():
+    """3000^2 (2^3 3 5^3) FP32, batch 2 in one call: the whole second field
+    against the oracle (the bench's 3000^2 workload)."""
+    kw = dict(ell=0.05, nu=2.5)
+    g = _api().GRF((3000, 3000), (1.0, 1.0), family="matern", precision="fp32", max_batch=2, **kw)
+    f = g.sample(seed=40, batch=2)[1].cpu().numpy()
+    ref = O.alg2_field((3000, 3000), (1.0, 1.0), _ospec("matern", **kw), 41)
+    _compare(f, ref)
+    g.close()
+
+
 def test_fp32_mixed_plan_has_no_adjoint_or_rfft():
     from paper_1105_2737_gb300 import _lib as L
     g = _api().GRF((12, 20), (1.0, 1.0), precision="fp32", max_batch=1)
