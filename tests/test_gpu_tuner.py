@@ -158,3 +158,29 @@ def test_forced_compile_time_geometries_3d(tmp_path):
     ref = O.sample(shape, Lb, O.Spectrum(O.MATERN, 1.0, 0.05, 1.5), 13, batch)
     rel = np.linalg.norm(f - ref) / np.linalg.norm(ref)
     assert rel <= 2e-6 and np.abs(f - ref).max() <= 1e-5 * np.sqrt((ref ** 2).mean()), rel
+
+
+def test_full_size_in_the_bench_schedule(tmp_path):
+    """4096^2 x 64 in the schedule the tuner picks for the bench on GB300
+    (T = 4, one column pair and two rows per CTA, radix 16, the compile-time
+    forms): sampled rows of two fields against the oracle's rows."""
+    from paper_1105_2737_gb300 import api
+    shape, Lb, batch = (4096, 4096), (1.0, 1.0), 64
+    path = tmp_path / "tune.txt"
+    path.write_text(_key2(shape, 2, batch) + " 4 16 1 16 1 16 2 1 0\n")
+    os.environ["GRF_TUNE_CACHE"] = str(path)
+    try:
+        g = api.GRF(shape, Lb, ell=0.05, nu=2.5, max_batch=batch)
+    finally:
+        del os.environ["GRF_TUNE_CACHE"]
+    sch = g.schedule
+    assert (sch["T"], sch["colA_P"], sch["colA_C"], sch["row_P"], sch["row_C"]) == (4, 16, 1, 16, 2)
+    f = g.sample(seed=640, batch=batch)
+    spec = O.Spectrum(O.MATERN, 1.0, 0.05, 2.5)
+    rows = [(0,), (3,), (2048,), (4095,)]
+    for b in (0, 63):
+        ref = O.field_lines(O.alg2_halfspectrum(shape, Lb, spec, 640 + b), shape, rows)
+        got = np.stack([f[(b,) + J].cpu().numpy() for J in rows]).astype(np.float64)
+        rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert rel <= 2e-6 and np.abs(got - ref).max() <= 1e-5, rel
+    g.close()
