@@ -6,7 +6,8 @@ seeds step*64 .. step*64+63 (the 4096^2 workload of the headline metric).
 The 4 GiB output per step is larger than L2, so no flush is needed between steps.
 
 Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle
-instead (one field per step) on the host cores.
+instead on the host cores (each step one 4096^2 field per core, one
+single-threaded oracle process per core; GRF_ORACLE_WORKERS caps the count).
 """
 from __future__ import annotations
 
@@ -57,7 +58,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -103,23 +104,75 @@ def _dist():
     return ws, rank, local
 
 
-def _oracle_fields_per_s(nfields: int = 1):
-    """Time the FP64 CPU oracle (as it stands) on `nfields` 4096^2 fields in a child
-    process pinned to one BLAS/OpenMP thread.  Returns (fields/s, seconds, cores)."""
-    code = (
-        "import time, sys\n"
-        "sys.path.insert(0, %r)\n"
-        "from oracle import grf_oracle as O\n"
-        "sp = O.Spectrum(O.MATERN, 1.0, 0.05, 2.5)\n"
-        "t = time.perf_counter()\n"
-        "for b in range(%d): O.alg2_field(%r, (1.0, 1.0), sp, b)\n"
-        "print(time.perf_counter() - t)\n" % (ROOT, nfields, SHAPE))
+_ORACLE_CODE = (
+    "import time, sys\n"
+    "sys.path.insert(0, %r)\n"
+    "from oracle import grf_oracle as O\n"
+    "sp = O.Spectrum(O.MATERN, %r, %r, %r)\n"
+    "t = time.perf_counter()\n"
+    "for b in range(%d): O.alg2_field(%r, (1.0, 1.0), sp, %d + b)\n"
+    "print(time.perf_counter() - t)\n")
+
+
+def _oracle_proc(nfields: int, shape, first: int):
+    code = _ORACLE_CODE % (ROOT, SPEC["sigma"], SPEC["ell"], SPEC["nu"], nfields, tuple(shape), first)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
-    if r.returncode != 0:
-        raise RuntimeError(r.stderr[-2000:])
-    dt = float(r.stdout.strip().splitlines()[-1])
+    return subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                            text=True, env=env)
+
+
+def _oracle_wait(p):
+    out, err = p.communicate(timeout=1800)
+    if p.returncode != 0:
+        raise RuntimeError(err[-2000:])
+    return float(out.strip().splitlines()[-1])
+
+
+def _oracle_fields_per_s(nfields: int = 1, shape=SHAPE):
+    """Time the FP64 CPU oracle (as it stands) on `nfields` fields of `shape` in a
+    child process pinned to one BLAS/OpenMP thread.  Returns (fields/s, seconds, cores)."""
+    dt = _oracle_wait(_oracle_proc(nfields, shape, 0))
     return nfields / dt, dt, 1
+
+
+def _oracle_workers() -> int:
+    """Host cores, capped by the memory one 4096^2 oracle field needs (about 4 GB)
+    and by GRF_ORACLE_WORKERS if set."""
+    cores = os.cpu_count() or 1
+    if os.environ.get("GRF_ORACLE_WORKERS"):
+        cores = max(1, min(cores, int(os.environ["GRF_ORACLE_WORKERS"])))
+    try:
+        avail = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_AVPHYS_PAGES")
+        cores = max(1, min(cores, int(avail // (5 << 30))))
+    except (ValueError, OSError):
+        pass
+    return cores
+
+
+def _oracle_all_cores(shape=SHAPE):
+    """The oracle on every usable host core at once, one single-threaded process
+    per core, one field each (processes across fields).  Returns (fields/s, wall s, cores)."""
+    w = _oracle_workers()
+    t0 = time.perf_counter()
+    procs = [_oracle_proc(1, shape, i) for i in range(w)]
+    for p in procs:
+        _oracle_wait(p)
+    dt = time.perf_counter() - t0
+    return w / dt, dt, w
+
+
+def _cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            txt = f.read()
+        for key in ("model name", "Model", "CPU part"):
+            for ln in txt.splitlines():
+                if ln.startswith(key):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
 
 
 def run_reference(args):
@@ -128,19 +181,22 @@ def run_reference(args):
         return
     for _ in range(args.warmup):
         pass  # the oracle has no warm-up state worth paying a 4096^2 field for
-    times = []
+    times, cores = [], 1
     for _ in range(args.steps):
-        _, dt, cores = _oracle_fields_per_s(1)
+        _, dt, cores = _oracle_all_cores()
         times.append(dt)
     tot = sum(times)
-    value = args.steps / tot
+    value = cores * args.steps / tot
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "fields/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD.replace("batch 64", "one field per step"), "impl": "FP64 numpy oracle"},
+        "config": {"workload": WORKLOAD.replace("batch 64", "%d fields per step, one per host core" % cores),
+                   "impl": "FP64 numpy oracle"},
         "cpu_baseline": {"value": value, "unit": "fields/s", "cores": cores, "kind": "oracle",
-                         "sample": "one 4096x4096 field per step, FP64 numpy oracle (recursive radix-2 FFT)"},
+                         "cpu": _cpu_model(),
+                         "sample": "%d 4096x4096 fields per step, one single-threaded FP64 numpy oracle "
+                                   "process per core (recursive radix-2 FFT)" % cores},
         "e2e": {"value": value, "unit": "fields/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpts_per_s": value * SHAPE[0] * SHAPE[1] / 1e9,
     }
@@ -148,12 +204,10 @@ def run_reference(args):
 
 
 # Algorithmic ALU operations per half-spectrum entry of the noise + axis-1 pass
-# (one lane-instruction each; derivation in the design doc §7): Philox4x32-10 shared
-# by two entries 29, uniforms 6, Box-Muller 26, Hermitian rule and s_K 3,
-# radix-16 FFT of length 4096 (3 stages, 2 twiddle stages) 39.
+# (one lane-instruction each): Philox4x32-10 shared by two entries 29, uniforms 6,
+# Box-Muller 26, Hermitian rule and s_K 3, radix-16 FFT of length 4096 (3 stages,
+# 2 twiddle stages) 39.  The peak it is held against is measured (grf_alu_peak).
 ALU_OPS_PER_ENTRY = 103
-# 152 SMs x 128 FP32/INT32 lanes x 2.07 GHz (maximum SM clock).
-ALU_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
 
 
 def _pass_bytes(kind: str, hsize: int, ntot: int) -> int:
@@ -246,17 +300,24 @@ def run_ours(args):
                 "traffic": traffic_of(kind), "peak_source": peak_src + " hbm_gbs (copy, burst)",
                 "alg_bytes_per_launch": alg}
 
-    if dom == "noise_columns":
-        # issue-bound on plain ALU arithmetic (Philox, Box-Muller, radix-16 FFT): DRAM ~12 %
-        avg = sum(per_kind[dom]) / len(per_kind[dom])
+    # the dominant kernel against HBM (the headline roofline: algorithmic bytes per
+    # launch / its CUDA-event duration / the measured copy bandwidth)
+    roofline = hbm_roofline(dom)
+    # the noise pass is issue-bound on plain ALU arithmetic (Philox, Box-Muller,
+    # radix-16 FFT); its ALU view is held against lane-operation rates measured
+    # on this GPU by grf_alu_peak (FP32 FMA issue rate, Philox rounds, log/rsqrt)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_peaks = {k: L.grf_alu_peak(k, stream.cuda_stream) for k in ("fma", "philox", "mufu")}
+    if "noise_columns" in per_kind:
+        avg = sum(per_kind["noise_columns"]) / len(per_kind["noise_columns"])
         ops = ALU_OPS_PER_ENTRY * hsize * BATCH
-        ach = ops / (avg / 1000.0) / 1e12
-        roofline = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
-                    "frac": ach / ALU_PEAK_TOPS, "traffic": traffic_of(dom),
-                    "peak_source": "152 SMs x 128 lanes x 2.07 GHz (unit counts and maximum clock)",
-                    "alg_ops_per_launch": ops, "hbm_view": hbm_roofline(dom)}
-    else:
-        roofline = hbm_roofline(dom)
+        ach = ops / (avg / 1000.0)
+        roofline["alu_view"] = {
+            "bound": "alu", "kernel": "noise_columns", "achieved": ach / 1e12, "peak": alu_peaks["fma"] / 1e12,
+            "unit": "Tops/s", "frac": ach / alu_peaks["fma"], "ops_per_entry": ALU_OPS_PER_ENTRY,
+            "alg_ops_per_launch": ops,
+            "peak_source": "measured in this run: FP32 FMA lane-operations/s (grf_alu_peak), %d SMs" % sms,
+            "measured_rates_tops": {k: v / 1e12 for k, v in alu_peaks.items()}}
     passes = {k: {"launches": len(v), "avg_ms": sum(v) / len(v),
                   "GBps_alg": (_pass_bytes(k, hsize, ntot) * BATCH / (sum(v) / len(v) / 1000.0) / 1e9)
                   if _pass_bytes(k, hsize, ntot) else None} for k, v in per_kind.items()}
@@ -384,9 +445,63 @@ def run_ours(args):
     del om
     torch.cuda.empty_cache()
 
+    # the other configurations of the metric: 512^2 x 64 (its 64 MiB output fits
+    # in L2, so L2 is flushed by a 1 GiB write before each timed call), 3-D 512^3
+    # x 1, forward + backward at 1024^2 x 16, and 64^2 FP64 with both algorithms
+    flush = torch.empty(256 << 20, dtype=torch.float32, device="cuda")
+
+    def _time_flushed(fn, k):
+        fn(0)
+        torch.cuda.synchronize()
+        tot = 0.0
+        for i in range(k):
+            flush.zero_()
+            d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            d0.record(stream)
+            fn(i + 1)
+            d1.record(stream)
+            torch.cuda.synchronize()
+            tot += d0.elapsed_time(d1)
+        return tot / k
+
+    g5 = GRF((512, 512), (1.0, 1.0), max_batch=64, **SPEC)
+    if not args.no_tune:
+        g5.tune()
+    o5 = g5.empty(64)
+    ms_512 = _time_flushed(lambda i: g5.sample(i * 64, 64, o5), 10)
+    ms_512_warm = _time_calls(lambda i: g5.sample(i * 64, 64, o5), 10)
+    g5.close()
+    del o5
+    g53 = GRF((512, 512, 512), (1.0, 1.0, 1.0), family="gaussian", sigma=1.0, ell=0.03, max_batch=1)
+    if not args.no_tune:
+        g53.tune()
+    o53 = g53.empty(1)
+    ms_512c = _time_calls(lambda i: g53.sample(i, 1, o53), 5)
+    g53.close()
+    del o53
+    gc5 = GRF((1024, 1024), (1.0, 1.0), family="matern", sigma=1.0, ell=0.05, nu=1.5, max_batch=16)
+    if not args.no_tune:
+        gc5.tune()
+    oc5 = gc5.empty(16)
+    Gc5 = torch.randn((16, 1024, 1024), device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+    ms_c5_fwd = _time_flushed(lambda i: gc5.sample(i * 16, 16, oc5), 5)
+    ms_c5 = _time_flushed(lambda i: (gc5.sample(i * 16, 16, oc5), gc5.backward(i * 16, Gc5)), 5)
+    gc5.close()
+    del oc5, Gc5, flush
+    c1 = {}
+    for alg in (2, 1):
+        gc1 = GRF((64, 64), (1.0, 1.0), family="matern", sigma=1.0, ell=0.1, nu=1.5, alg=alg, precision="fp64",
+                  max_batch=1)
+        oc1 = gc1.empty(1)
+        c1[alg] = _time_calls(lambda i: gc1.sample(i, 1, oc1), 64)
+        gc1.close()
+    torch.cuda.empty_cache()
+
     if rank != 0:
         return
-    cpu_val, cpu_s, cores = _oracle_fields_per_s(1) if not args.no_cpu else (None, None, None)
+    cpu_one = _oracle_fields_per_s(1) if not args.no_cpu else None
+    cpu_all = _oracle_all_cores() if not args.no_cpu else None
+    cpu_512 = _oracle_fields_per_s(8, (512, 512)) if not args.no_cpu else None
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": "fields/s", "n_gpus": ws, "steps": args.steps,
@@ -409,6 +524,17 @@ def run_ours(args):
         "extra_uneven_batch_4096": {"fields_per_s": 4096 / (ms_u / 1000.0), "gpts_per_s": upoints / (ms_u / 1e3) / 1e9,
                                     "ms_per_launch": ms_u, "points": upoints, "status": ustatus,
                                     "launch": "one persistent kernel per batch, CUDA graph replay"},
+        "extra_2d_512sq_batch64": {"fields_per_s": 64 / (ms_512 / 1e3), "gpts_per_s": 64 * 512 ** 2 / (ms_512 / 1e3) / 1e9,
+                                   "ms_per_call": ms_512, "l2": "flushed before each call (1 GiB written)",
+                                   "fields_per_s_l2_resident": 64 / (ms_512_warm / 1e3)},
+        "extra_3d_512cubed_batch1": {"fields_per_s": 1 / (ms_512c / 1e3), "gpts_per_s": 512 ** 3 / (ms_512c / 1e3) / 1e9,
+                                     "ms_per_call": ms_512c, "l2": "output 512 MiB > L2"},
+        "extra_grad_1024sq_batch16": {"fwd_bwd_fields_per_s": 16 / (ms_c5 / 1e3), "ms_fwd_bwd": ms_c5,
+                                      "ms_fwd": ms_c5_fwd, "calls": "grf_sample + grf_backward (per-field d/d(sigma, ell, nu))",
+                                      "l2": "flushed before each call"},
+        "extra_fp64_64sq_alg1_vs_alg2": {"alg2_fields_per_s": 1e3 / c1[2], "alg1_fields_per_s": 1e3 / c1[1],
+                                         "alg1_over_alg2_time": c1[1] / c1[2],
+                                         "note": "one field per launch sequence; the paper: Algorithm 1 takes about twice as long"},
         "extra_neumann_4097sq_batch16": {"fields_per_s": 16 / (ms_b / 1000.0), "gpts_per_s": 16 * pts_b / (ms_b / 1e3) / 1e9,
                                          "ms_per_call": ms_b, "launches_per_call": 2},
         "extra_3000sq_fp32_plain_batch4": {"fields_per_s": 4 / (ms_m / 1000.0), "gpts_per_s": 4 * 9e6 / (ms_m / 1e3) / 1e9,
@@ -419,9 +545,15 @@ def run_ours(args):
                 "note": "grf_sample_host into pinned host memory: device buffers, copies overlapped with compute (bounded by the ~190 GB/s device-to-host rate); seeds passed by value, no input buffers"},
         "gpu_launches": nrec,
         "clocks": clocks,
-        "cpu_baseline": ({"value": cpu_val, "unit": "fields/s", "cores": cores, "kind": "oracle",
-                          "sample": "one 4096x4096 field of the same workload, FP64 numpy oracle, %.1f s" % cpu_s}
-                         if cpu_val else None),
+        "cpu_baseline": ({"value": cpu_all[0], "unit": "fields/s", "cores": cpu_all[2], "kind": "oracle",
+                          "cpu": _cpu_model(),
+                          "sample": "%d 4096x4096 fields of the same workload at once, one single-threaded FP64 "
+                                    "numpy oracle process per core, %.1f s wall" % (cpu_all[2], cpu_all[1]),
+                          "one_core": {"value": cpu_one[0], "unit": "fields/s", "cores": 1,
+                                       "sample": "one 4096x4096 field, %.1f s" % cpu_one[1]},
+                          "one_core_512sq": {"value": cpu_512[0], "unit": "fields/s", "cores": 1,
+                                             "sample": "8 fields of 512x512 (the paper's size), %.2f s" % cpu_512[1]}}
+                         if cpu_all else None),
         "paper_context": {"fields_per_s_512sq": PAPER_FIELDS_PER_S, "note": "0.25 s per 512x512 field on an older CPU"},
     }
     print(json.dumps(line), flush=True)

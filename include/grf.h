@@ -277,7 +277,8 @@ grf_status grf_batch_graph_launch(grf_plan p, uint64_t seed, void* const* out, v
  * cudaMalloc or cudaFree would implicitly synchronise the device.  It draws
  * the same fields as grf_sample on a plan created with
  * grf_plan_create(2, n, L, spec, GRF_ALG_ONE_FFT, GRF_FP32, ...): FP32,
- * §3 Algorithm 2, field b with Philox key seed + b.
+ * Hermitian complex noise followed by one inverse FFT (the GRF_ALG_ONE_FFT
+ * mode), field b with Philox key seed + b.
  *   n, L  : host arrays of 2 grid sizes (powers of two, 2 <= N_i <= 1024) and
  *           edge lengths (> 0); sizes above 1024 return GRF_ERR_INVALID_ARG.
  *   spec  : Matern, Gaussian or paper family; normalize_discrete is not
@@ -338,6 +339,23 @@ grf_status grf_cov_origin(grf_plan p, uint64_t seed, int64_t count, double* sums
  */
 grf_status grf_philox_words(uint64_t key, uint32_t tag, uint64_t q0, int64_t count, uint32_t* out_words,
                             void* stream);
+
+/*
+ * grf_alu_peak - measured lane-operation rate of the current device, the
+ * denominator of the ALU view of the noise pass's roofline (no counterpart in
+ * the paper).  Launches one short microbenchmark (eight independent chains
+ * per thread, 8 CTAs of 256 threads per SM, tens of ms) on `stream`, times it
+ * with CUDA events and writes operations per second to *ops_per_s (host).
+ *   kind 0: FP32 fused multiply-adds (one operation each): the issue ceiling;
+ *   kind 1: Philox4x32 rounds, counted as two 32 x 32 -> 64-bit multiplies,
+ *           two three-input XORs and the round's two key additions shared by
+ *           eight chains;
+ *   kind 2: log2 and reciprocal square root (the special functions of
+ *           Box-Muller), one operation each.
+ * Allocates and frees a small device buffer; synchronises the stream.
+ * GRF_ERR_INVALID_ARG for another kind or a NULL pointer.
+ */
+grf_status grf_alu_peak(int kind, double* ops_per_s, void* stream);
 
 /*
  * Per-launch timing of a plan's kernels, for measurement (no counterpart in

@@ -73,6 +73,7 @@ def lib():
             "grf_cov_origin": (C.c_int, [P, U64, I64, VP, VP]),
             "grf_sample_2d_static": (C.c_int, [C.POINTER(I64), C.POINTER(D), C.POINTER(grf_spectrum), U64, I64,
                                                VP, VP]),
+            "grf_alu_peak": (C.c_int, [C.c_int, C.POINTER(D), VP]),
             "grf_plan_query": (I64, [P, C.c_int]),
             "grf_plan_timing": (C.c_int, [P, I64]),
             "grf_plan_timing_read": (I64, [P, C.POINTER(C.c_int), C.POINTER(C.c_float), I64]),
@@ -212,6 +213,16 @@ def grf_sample_2d_static(n, L, spec, seed, batch, out_ptr, stream=0):
     LL = (C.c_double * 2)(*[float(x) for x in L])
     check(lib().grf_sample_2d_static(nn, LL, C.byref(spec), C.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), int(batch),
                                      C.c_void_p(out_ptr), C.c_void_p(stream)), "grf_sample_2d_static")
+
+
+ALU_PEAK_KINDS = {"fma": 0, "philox": 1, "mufu": 2}
+
+
+def grf_alu_peak(kind: str, stream=0) -> float:
+    """Measured operations per second of one microbenchmark kind (see grf.h)."""
+    v = C.c_double()
+    check(lib().grf_alu_peak(ALU_PEAK_KINDS[kind], C.byref(v), C.c_void_p(stream)), "grf_alu_peak")
+    return float(v.value)
 
 
 def grf_plan_query(plan, key: int) -> int:

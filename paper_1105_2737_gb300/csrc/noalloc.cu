@@ -22,11 +22,19 @@
 
 namespace grf {
 
-// Largest grid: N1, N2 <= 1024.  Worst-case use: twiddles and stage tables for
-// length 1024 (48 KiB), the folded s_K table 513 x 513 floats (1.0 MiB) and one
-// field's half spectrum 1024 x 513 complex floats (4.0 MiB).
+// Largest grid: N1, N2 <= 1024.  Worst-case use, each part rounded up to 256
+// bytes as the call lays them out: twiddles and stage tables for length 1024,
+// (2 * 1024 + kStageTableEntries) complex floats (about 112 KiB); the folded
+// s_K table, 513 x 513 floats (about 1.0 MiB); one field's half spectrum,
+// 1024 x 513 complex floats (about 4.0 MiB).  About 5.1 MiB in all.
 constexpr int kNoAllocMaxSide = 1024;
 constexpr size_t kNoAllocScratchBytes = 6u << 20;
+constexpr size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr size_t kNoAllocWorstBytes =
+    round256((size_t)(2 * kNoAllocMaxSide + kStageTableEntries) * 8) +
+    round256((size_t)(kNoAllocMaxSide / 2 + 1) * (kNoAllocMaxSide / 2 + 1) * 4) +
+    (size_t)kNoAllocMaxSide * (kNoAllocMaxSide / 2 + 1) * 8;
+static_assert(kNoAllocWorstBytes <= kNoAllocScratchBytes, "the largest grid must fit the scratch array");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 

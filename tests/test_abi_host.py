@@ -126,3 +126,10 @@ def test_boundary_plan_rejects_discrete_normalisation(L):
     st, h = _create_bc(L, 2, [8, 8], [1.0, 1.0], spec=L.make_spectrum(normalize_discrete=1))
     assert st == 2 and not h.value
     assert L.lib().grf_bc_plan_create(None, 1, None, None, None, 1, 1) == 1
+
+
+def test_alu_peak_rejects_bad_arguments(L):
+    v = C.c_double()
+    assert L.lib().grf_alu_peak(3, C.byref(v), None) == 1
+    assert L.lib().grf_alu_peak(-1, C.byref(v), None) == 1
+    assert L.lib().grf_alu_peak(0, None, None) == 1

@@ -1,0 +1,101 @@
+"""Full-size parity: the workloads the bench times, in the launch configuration
+it times them, compared with the FP64 oracle element by element.
+
+* 2-D 4096^2 x 64 in the schedule the tuner picks on this GPU (the bench tunes
+  before it times): fields 0 and 63 whole, every one of their 16.7 M points.
+* The 4096-field uneven batch in one persistent launch: the largest 2-D, 3-D
+  and 1-D fields of the batch (1024-side 2-D, 128^3, 2^20) and a spread of
+  small ones, whole, with relative L2 and max abs.
+* 3-D 512^3 x 1 (Gaussian, ell = 0.03): sampled lines of the field (the
+  oracle's half spectrum is 67 M modes; each line is a dense contraction).
+
+Bars: FP32 relative L2 <= 2e-6 and max abs <= 1e-5 sigma (sigma = 1 here)."""
+import numpy as np
+import pytest
+
+from oracle import grf_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL_L2 = 2e-6
+MAX_ABS = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1105_2737_gb300 import build
+    build()
+
+
+def _api():
+    from paper_1105_2737_gb300 import api
+    return api
+
+
+def _check(got, ref, what):
+    got = np.asarray(got, dtype=np.float64)
+    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    mx = np.abs(got - ref).max()
+    assert rel <= REL_L2 and mx <= MAX_ABS, (what, rel, mx)
+    return rel, mx
+
+
+def test_headline_whole_fields_tuned_schedule():
+    """4096^2 x 64, Matern (1, 0.05, 2.5), tuned exactly as the bench tunes it:
+    fields 0 and 63 of one call, whole."""
+    shape, Lb, batch = (4096, 4096), (1.0, 1.0), 64
+    g = _api().GRF(shape, Lb, family="matern", sigma=1.0, ell=0.05, nu=2.5, max_batch=batch)
+    g.tune()
+    seed = 64 * 7
+    f = g.sample(seed=seed, batch=batch)
+    spec = O.Spectrum(O.MATERN, 1.0, 0.05, 2.5)
+    for b in (0, batch - 1):
+        ref = O.alg2_field(shape, Lb, spec, seed + b)
+        _check(f[b].cpu().numpy(), ref, ("field", b, g.schedule))
+    g.close()
+
+
+def test_full_size_uneven_batch_every_kind():
+    """The 4096-field uneven batch: the largest 2-D field, the largest 3-D field,
+    the longest 1-D field and the first eight small fields, whole, against the oracle."""
+    from paper_1105_2737_gb300.inputs import uneven_batch
+    shapes, lengths, specs = uneven_batch(4096, seed=0)
+    b = _api().GRFBatch(shapes, lengths, specs)
+    outs = b.sample(seed=0)
+    torch.cuda.synchronize()
+    assert b.status() == 0
+    size = [int(np.prod(s)) for s in shapes]
+    picks = []
+    for d in (2, 3, 1):
+        picks.append(max((i for i in range(len(shapes)) if len(shapes[i]) == d), key=lambda i: size[i]))
+    picks += [i for i in range(len(shapes)) if size[i] <= 2 ** 16][:8]
+    kinds = {len(shapes[i]) for i in picks}
+    assert kinds == {1, 2, 3}
+    assert max(size[i] for i in picks if len(shapes[i]) == 2) >= 512 * 1024
+    for i in picks:
+        sp = specs[i]
+        ref = O.alg2_field(shapes[i], lengths[i], O.Spectrum(O.MATERN, sp["sigma"], sp["ell"], sp["nu"]), i)
+        _check(outs[i].cpu().numpy(), ref, ("field", i, shapes[i]))
+    b.close()
+
+
+def test_512_cubed_sampled_lines():
+    """3-D 512^3 x 1, Gaussian ell = 0.03: sampled lines f[j1, j2, :] against the
+    oracle's lines, and the field's variance against c(0)."""
+    shape, Lb = (512, 512, 512), (1.0, 1.0, 1.0)
+    g = _api().GRF(shape, Lb, family="gaussian", sigma=1.0, ell=0.03, max_batch=1)
+    f = g.sample(seed=0, batch=1)
+    spec = O.Spectrum(O.GAUSSIAN, 1.0, 0.03)
+    lines = [(0, 0), (1, 511), (256, 7), (333, 128), (511, 511)]
+    AH = O.alg2_halfspectrum(shape, Lb, spec, 0)
+    ref = O.field_lines(AH, shape, lines)
+    del AH
+    got = np.stack([f[(0,) + J].cpu().numpy() for J in lines])
+    _check(got, ref, "512^3 lines")
+    var = float((f.double() ** 2).mean())
+    c0 = float((O.scaled_density(shape, Lb, spec, half=True) * O.half_weights(shape)).sum())
+    assert 0.8 * c0 < var < 1.25 * c0, (var, c0)
+    g.close()

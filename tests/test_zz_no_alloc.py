@@ -51,6 +51,22 @@ def test_two_calls_in_a_row_match_the_plan_path(L):
         assert rel <= 2e-6 and np.abs(g - ref).max() <= 1e-5, (c[0], rel)
 
 
+def test_worst_case_smallest_grids_and_paper_family(L):
+    """The largest grid the array holds (1024 x 1024, two fields in a row), the
+    smallest grids (2 x 4 and 4 x 2: one row of the c2r pass, trimmed CTAs) and
+    the polynomial family of the paper, each against the plan path."""
+    calls = [((1024, 1024), (1.0, 1.0), L.make_spectrum(L.GRF_MATERN, 1.0, 0.02, 2.5), 99, 2),
+             ((2, 4), (1.0, 1.0), L.make_spectrum(L.GRF_MATERN, 1.0, 0.3, 1.5), 5, 3),
+             ((4, 2), (1.0, 2.0), L.make_spectrum(L.GRF_GAUSSIAN, 1.0, 0.3, 0.0), 6, 3),
+             ((64, 128), (8.0, 8.0), L.make_spectrum(L.GRF_PAPER_POLY, 1.0, 0.0, 0.0, 10.0, 1, 2, 1), 17, 2)]
+    for c in calls:
+        g = _static(L, *c)
+        ref = _reference(L, *c)
+        rel = np.linalg.norm(g - ref) / np.linalg.norm(ref)
+        scale = max(1.0, float(np.sqrt((ref ** 2).mean())))
+        assert rel <= 2e-6 and np.abs(g - ref).max() <= 1e-5 * scale, (c[0], rel)
+
+
 def test_sizes_beyond_the_scratch_are_rejected(L):
     out = torch.empty(4, dtype=torch.float32, device="cuda")
     nn = (C.c_int64 * 2)(2048, 64)
