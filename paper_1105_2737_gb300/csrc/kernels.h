@@ -144,6 +144,9 @@ cudaError_t launch_col_noise(int P, const ColArgs& a, dim3 grid, cudaStream_t s)
 // Compile-time-geometry forms (spec_*.cu): launch and return true if the
 // launch has one, else return false and launch nothing.
 bool launch_col_noise_spec(int P, const ColArgs& a, dim3 grid, cudaStream_t s, cudaError_t* err);
+// The 2-D noise pair pass specialised for those geometries and the tile T
+// (noise_fast.cu): launch and return true if the launch has that form.
+bool launch_noise_pair_fast(int P, const ColArgs& a, dim3 grid, cudaStream_t s, cudaError_t* err);
 bool launch_col_load_pair_spec(int P, const ColArgs& a, dim3 grid, cudaStream_t s, cudaError_t* err);
 bool launch_row_c2r_spec(int P, const RowArgs& a, dim3 grid, cudaStream_t s, cudaError_t* err);
 // Grid-stride forms (ctas CTAs walk all tiles) of the noise + axis-1 pass and the c2r pass.
