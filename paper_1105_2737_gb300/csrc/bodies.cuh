@@ -411,7 +411,7 @@ GRF_DEV float2 r2c_post(float2 Zk, float2 Zmk, float2 w) {
 
 // LN, CC: a compile-time length M = 2^LN and CC rows per CTA (see
 // pass_kernels.cuh); 0 takes them from the launch descriptor.
-template <int P, int SRC, int MODE, int LN = 0, int CC = 0>
+template <int P, int SRC, int MODE, int LN = 0, int CC = 0, int TT = 0>
 GRF_DEV void row_body(const RowArgs& a, int64_t bx, int nthr_rt, float2* sm) {
   const int C = CC ? CC : a.C;
   const int nthr = (LN && CC) ? CC * (1 << LN) / P : nthr_rt;
@@ -431,10 +431,12 @@ GRF_DEV void row_body(const RowArgs& a, int64_t bx, int nthr_rt, float2* sm) {
   if constexpr (MODE == ROW_C2R && SRC == ROW_LOAD_Z) {
     // Z[0..M-1] of the c2r split, formed by the last column pass: straight
     // into the M-point inverse FFT.
-    const float2* src = a.inH + hrow_base(valid ? g : 0, M, a.logT);
+    // TT: a compile-time tile (the loads then differ by constant offsets)
+    const int logT = TT ? ilog2c(TT) : a.logT;
+    const float2* src = a.inH + hrow_base(valid ? g : 0, M, logT);
 #pragma unroll
     for (int q = 0; q < P; ++q)
-      v[q] = valid ? __ldcg(src + ((int64_t)(tau + TPT * q) << a.logT)) : make_float2(0.f, 0.f);
+      v[q] = valid ? __ldcg(src + ((int64_t)(tau + TPT * q) << logT)) : make_float2(0.f, 0.f);
     fft_core<P, +1>(v, sm, tau, c, C, M, logM, a.twM, a.tws, nthr);
     if (valid) {
       float2* o = reinterpret_cast<float2*>(a.outR + g * N);

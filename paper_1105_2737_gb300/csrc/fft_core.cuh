@@ -14,6 +14,7 @@
 #pragma once
 #include <type_traits>
 #include "common.cuh"
+#include "kernels.h"
 
 namespace grf {
 
@@ -134,15 +135,23 @@ GRF_DEV float2 tw_load(const float2* __restrict__ tw, int k, int dir) {
 
 // One final stage of radix R < P: each thread does P/R butterflies j = tau + u TPT
 // on registers v[u + r P/R]; Ns = N/R so the twiddle is exp(DIR 2 pi i j r / N).
+// With radix-16 stages before it (P = 16, Ns = 16 or 256) the twiddles come
+// from the small-stage table, entry (r - 1) Ns + j (lanes with consecutive j
+// read consecutive entries); otherwise from tw[j r].
 template <int P, int R, int DIR>
-GRF_DEV void last_small_stage(float2 (&v)[P], int tau, int TPT, const float2* __restrict__ tw) {
+GRF_DEV void last_small_stage(float2 (&v)[P], int tau, int TPT, const float2* __restrict__ tw,
+                              const float2* __restrict__ tws) {
   constexpr int U = P / R;
+  const int Ns = TPT * U;
+  const bool table = P == 16 && (Ns == 16 || Ns == 256);
+  const float2* st = tws + (Ns == 16 ? small_stage_offset(R, 16) : small_stage_offset(R, 256));
   static_for<0, U>([&](auto uu) {
     constexpr int u = decltype(uu)::value;
     const int j = tau + u * TPT;
     static_for<1, R>([&](auto rr) {
       constexpr int r = decltype(rr)::value;
-      v[u + r * U] = cmul(v[u + r * U], tw_load(tw, j * r, DIR));
+      const float2 w = table ? tw_load(st, (r - 1) * Ns + j, DIR) : tw_load(tw, j * r, DIR);
+      v[u + r * U] = cmul(v[u + r * U], w);
     });
     dft_regs<R, DIR, U, u>(v);
   });
@@ -241,13 +250,13 @@ GRF_DEV void fft_core(float2 (&v)[P], float2* sm, int tau, int c, int C, int N, 
       Ns *= P;
     }
     if constexpr (P >= 4) {
-      if (rl == 1) last_small_stage<P, 2, DIR>(v, tau, TPT, tw);
+      if (rl == 1) last_small_stage<P, 2, DIR>(v, tau, TPT, tw, tws);
     }
     if constexpr (P >= 8) {
-      if (rl == 2) last_small_stage<P, 4, DIR>(v, tau, TPT, tw);
+      if (rl == 2) last_small_stage<P, 4, DIR>(v, tau, TPT, tw, tws);
     }
     if constexpr (P >= 16) {
-      if (rl == 3) last_small_stage<P, 8, DIR>(v, tau, TPT, tw);
+      if (rl == 3) last_small_stage<P, 8, DIR>(v, tau, TPT, tw, tws);
     }
   }
 }

@@ -191,8 +191,18 @@ struct SpecParams {
 };
 // tw[L + k] = exp(2 pi i k / L) for powers of two L <= maxlen, then (at
 // offset 2 maxlen) the stage tables: radix 16 (spans 16, 256), radix 8 (8, 64,
-// 512), radix 4 (4, 16, 64, 256, 1024), (P - 1) Ns entries per span.
-constexpr int kStageTableEntries = 15 * (16 + 256) + 7 * (8 + 64 + 512) + 3 * (4 + 16 + 64 + 256 + 1024);
+// 512), radix 4 (4, 16, 64, 256, 1024), (P - 1) Ns entries per span; then the
+// tables of the final radix-2/4/8 stage of the radix-16 engine (spans 16 and
+// 256, see small_stage_offset).
+constexpr int kStageTableMain = 15 * (16 + 256) + 7 * (8 + 64 + 512) + 3 * (4 + 16 + 64 + 256 + 1024);
+constexpr int kSmallStageEntries = (1 + 3 + 7) * (16 + 256);
+constexpr int kStageTableEntries = kStageTableMain + kSmallStageEntries;
+// Offset (within the stage tables) of the final radix-R stage (R in {2, 4, 8})
+// after radix-16 stages of total span Ns (16 or 256): (R - 1) Ns entries,
+// entry (r - 1) Ns + j = exp(+2 pi i j r / (R Ns)), j < Ns, r = 1..R-1.
+__host__ __device__ constexpr int small_stage_offset(int R, int Ns) {
+  return kStageTableMain + (Ns == 16 ? 0 : 11 * 16) + (R == 2 ? 0 : (R == 4 ? Ns : 4 * Ns));
+}
 cudaError_t build_twiddles(float2* tw, int maxlen, cudaStream_t s);
 cudaError_t build_twiddles_d(double2* tw, int maxlen, cudaStream_t s);
 cudaError_t build_stab(float* stab, float* dstab, const SpecParams& sp, double dig_a_minus_nu,

@@ -22,10 +22,10 @@ __global__ void __launch_bounds__(kMaxThreads<P>, kMinBlocks<P>) col_kernel(ColA
   }
 }
 
-template <int P, int SRC, int MODE, int LN = 0, int CC = 0>
+template <int P, int SRC, int MODE, int LN = 0, int CC = 0, int TT = 0>
 __global__ void __launch_bounds__(kMaxThreads<P>, kMinBlocks<P>) row_kernel(RowArgs a) {
   extern __shared__ float2 sm[];
-  row_body<P, SRC, MODE, LN, CC>(a, blockIdx.x, blockDim.x, sm);
+  row_body<P, SRC, MODE, LN, CC, TT>(a, blockIdx.x, blockDim.x, sm);
 }
 
 // log2 N if (N, C) is one of the compile-time radix-16 geometries (C N = 4096,
@@ -85,7 +85,7 @@ static cudaError_t launch_col_t(const ColArgs& a, dim3 grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int P, int SRC, int MODE, int LN = 0, int CC = 0>
+template <int P, int SRC, int MODE, int LN = 0, int CC = 0, int TT = 0>
 static cudaError_t launch_row_t(const RowArgs& a, dim3 grid, cudaStream_t s) {
   const int threads = a.C * (a.M / P);
   size_t smem = row_smem_bytes(a.M, a.C);
@@ -93,7 +93,7 @@ static cudaError_t launch_row_t(const RowArgs& a, dim3 grid, cudaStream_t s) {
     const size_t need = (size_t)threads * 3 * sizeof(double);
     if (need > smem) smem = need;
   }
-  auto k = row_kernel<P, SRC, MODE, LN, CC>;
+  auto k = row_kernel<P, SRC, MODE, LN, CC, TT>;
   cudaError_t e = prepare_kernel((const void*)k, threads, smem);
   if (e != cudaSuccess) return e;
   k<<<grid, threads, smem, s>>>(a);

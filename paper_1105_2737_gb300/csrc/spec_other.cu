@@ -1,6 +1,6 @@
 // The axis-2 pair pass (3-D) and the c2r pass compiled for fixed radix-16
 // geometries: length 2^LN with 4096 / 2^LN columns or rows per CTA, 256
-// threads (see pass_kernels.cuh).
+// threads (see pass_kernels.cuh); the c2r pass also per workspace tile T.
 #include "pass_kernels.cuh"
 
 namespace grf {
@@ -11,9 +11,18 @@ template <int LN>
 cudaError_t load_pair_t(const ColArgs& a, dim3 grid, cudaStream_t s) {
   return launch_col_t<16, COL_LOAD, COL_INV, 1, NV_ANY, LN, (4096 >> LN)>(a, grid, s);
 }
+// the workspace tile T as a compile-time constant (T in {1, 2, 4, 8, 16})
 template <int LN>
 cudaError_t row_c2r_t(const RowArgs& a, dim3 grid, cudaStream_t s) {
-  return launch_row_t<16, ROW_LOAD_Z, ROW_C2R, LN, (4096 >> LN)>(a, grid, s);
+  constexpr int CC = 4096 >> LN;
+  switch (a.T) {
+    case 1: return launch_row_t<16, ROW_LOAD_Z, ROW_C2R, LN, CC, 1>(a, grid, s);
+    case 2: return launch_row_t<16, ROW_LOAD_Z, ROW_C2R, LN, CC, 2>(a, grid, s);
+    case 4: return launch_row_t<16, ROW_LOAD_Z, ROW_C2R, LN, CC, 4>(a, grid, s);
+    case 8: return launch_row_t<16, ROW_LOAD_Z, ROW_C2R, LN, CC, 8>(a, grid, s);
+    case 16: return launch_row_t<16, ROW_LOAD_Z, ROW_C2R, LN, CC, 16>(a, grid, s);
+    default: return launch_row_t<16, ROW_LOAD_Z, ROW_C2R, LN, CC>(a, grid, s);
+  }
 }
 
 }  // namespace

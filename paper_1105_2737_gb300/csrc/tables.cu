@@ -43,6 +43,17 @@ __global__ void twiddle_kernel_d(double2* tw, int total) {
 __global__ void stage_table_kernel(float2* tws) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= kStageTableEntries) return;
+  double sn, cs;
+  if (i >= kStageTableMain) {  // final small stages: span 16 (176 entries), then 256
+    const int Ns = i < kStageTableMain + 11 * 16 ? 16 : 256;
+    const int loc = i - (Ns == 16 ? kStageTableMain : kStageTableMain + 11 * 16);
+    const int R = loc < Ns ? 2 : (loc < 4 * Ns ? 4 : 8);
+    const int e = loc - (R == 2 ? 0 : (R == 4 ? Ns : 4 * Ns));
+    const int r = e / Ns + 1, j = e % Ns;
+    sincospi(2.0 * (double)(j * r) / (double)(R * Ns), &sn, &cs);
+    tws[i] = make_float2((float)cs, (float)sn);
+    return;
+  }
   const int R = i < 4080 ? 16 : (i < 8168 ? 8 : 4);
   int loc = i < 4080 ? i : (i < 8168 ? i - 4080 : i - 8168);
   int Ns = R;
@@ -51,7 +62,6 @@ __global__ void stage_table_kernel(float2* tws) {
     Ns *= R;
   }
   const int r = loc / Ns + 1, m = loc % Ns;
-  double sn, cs;
   sincospi(2.0 * (double)((int64_t)m * r) / (double)(R * Ns), &sn, &cs);
   tws[i] = make_float2((float)cs, (float)sn);
 }
