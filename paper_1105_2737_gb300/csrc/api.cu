@@ -163,6 +163,8 @@ struct grf_plan_s {
   // caller's stream, the others on tail_stream
   int pipe = 1;
   int row_tma = 0;  // c2r pass: 0 = row kernel, 1 = persistent kernel fed by bulk async copies
+  int plane_R = 0;  // 3-D: the plane path's axis-2 split N2 = R Q (0: the three-pass form)
+  int64_t ws_field = 0;  // workspace entries per field
   bool sched_cached = false;  // the schedule came from the tuning cache at creation
   int gs_ctas = 1;  // grid-stride CTAs per SM of each pass when pipelined (0: full grids)
   int num_sms = 0;
@@ -535,6 +537,31 @@ grf_status sample_chunk_fp32(grf_plan p, uint64_t seed, int64_t f0, int64_t nb, 
     else TLAUNCH(GRF_KERNEL_ROWS_1D, launch_row(ROW_NOISE_REAL, ROW_R2C_SCALE_C2R, p->row.P, r, row_grid(r), s), "1-D alg1");
     return GRF_OK;
   }
+  if (p->d == 3 && p->alg == 2 && p->plane_R) {
+    // the plane path: noise + axis 1 + the first radix-R step of axis 2, then
+    // one CTA per sub-plane for the rest of axis 2 and the c2r pass
+    PlaneArgs pl{};
+    pl.N1 = p->N1;
+    pl.N2 = p->Nmid;
+    pl.M = p->M;
+    pl.R = p->plane_R;
+    pl.Q = p->Nmid / p->plane_R;
+    pl.S3 = p->M + 2;
+    pl.ws = ws;
+    pl.out = out;
+    pl.tw = p->tw;
+    pl.tws = p->tw + 2 * p->twmax;
+    pl.status = p->status;
+    const ColArgs a = col_axis1(p, g, nullptr, ws, 1);
+    TLAUNCH(GRF_KERNEL_NOISE_COLUMNS, launch_plane3_noise(a, pl, nb, s), "3-D plane pass 1");
+    if (st && st != s) {
+      GRF_CUDA(cudaEventRecord(ev, s), "pipeline event");
+      GRF_CUDA(cudaStreamWaitEvent(st, ev, 0), "pipeline wait");
+      s = st;
+    }
+    TLAUNCH(GRF_KERNEL_ROWS_C2R, launch_plane3_c2r(pl, nb, s), "3-D plane pass 2");
+    return GRF_OK;
+  }
   const int T = p->d == 2 ? p->T : 1;
   const bool gs = st && st != s && p->gs_ctas > 0;
   if (p->alg == 2) {
@@ -828,7 +855,14 @@ grf_status grf_plan_create(grf_plan* out, int d, const int64_t* n, const double*
         while (p->T > 1 && p->N1 % p->T) p->T >>= 1;
       }
       p->chunk = max_batch;
-      PLAN_CUDA(dmalloc(&p->ws, (size_t)(p->chunk * p->hsize)), "workspace");
+      p->ws_field = p->hsize;
+      if (d == 3 && alg == GRF_ALG_ONE_FFT) {
+        const char* pe3 = std::getenv("GRF_PLANE3");  // "0": keep the three-pass form
+        if (!(pe3 && pe3[0] == '0')) p->plane_R = plane3_radix(p->N1, p->Nmid, p->M);
+        if (p->plane_R)
+          p->ws_field = std::max<int64_t>(p->hsize, (int64_t)plane3_ws_entries(p->N1, p->Nmid, p->M));
+      }
+      PLAN_CUDA(dmalloc(&p->ws, (size_t)(p->chunk * p->ws_field)), "workspace");
       {  // a tuned schedule for this GPU and problem, if one was stored
         std::vector<int> v;
         if (tune_cache_lookup(plan_key(p), &v)) p->sched_cached = apply_schedule(p, v);
@@ -925,7 +959,7 @@ grf_status grf_sample(grf_plan p, uint64_t seed, int64_t batch, void* out, void*
     int k = 0;
     for (int64_t f0 = 0; f0 < batch; f0 += per, ++k) {
       const int64_t nb = batch - f0 < per ? batch - f0 : per;
-      st = sample_chunk_fp32(p, seed, f0, nb, (float*)out + f0 * p->ntot, s, p->ws + f0 * p->hsize, p->tail_stream,
+      st = sample_chunk_fp32(p, seed, f0, nb, (float*)out + f0 * p->ntot, s, p->ws + f0 * p->ws_field, p->tail_stream,
                              p->pipe_ev[k % 8]);
       if (st != GRF_OK) return st;
     }
@@ -949,6 +983,7 @@ grf_status grf_plan_tune(grf_plan p, void* stream) {
     return fail(GRF_ERR_UNSUPPORTED, "the tuner covers FP32 2-D and 3-D plans on powers of two");
   const char* force = std::getenv("GRF_TUNE_FORCE");
   if (p->sched_cached && !(force && force[0] == '1')) return GRF_OK;  // already tuned on this GPU
+  if (p->plane_R) return GRF_OK;  // the 3-D plane path has one schedule
   cudaStream_t s = (cudaStream_t)stream;
   // enough fields for a few waves of CTAs, within max_batch
   int64_t bt = (int64_t)((64ll << 20) / p->ntot);
@@ -1407,6 +1442,7 @@ int64_t grf_plan_query(grf_plan p, int key) {
     case 13: return p->colB.P;
     case 14: return p->colB.C;
     case 15: return p->row_tma;
+    case 17: return p->plane_R;
     default: return -1;
   }
 }

@@ -22,59 +22,11 @@
 // (bounded again) for the CTA's copies still in flight, and the CTA returns.
 #include "grf.h"
 #include "bodies.cuh"
+#include "tma.cuh"
 
 namespace grf {
 
-namespace {
-
-constexpr unsigned kTmaSpinCap = 1u << 24;
-constexpr unsigned long long kTmaTimeoutNs = 2000000000ull;  // 2 s
-
-GRF_DEV unsigned long long tma_clock_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-GRF_DEV uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-GRF_DEV void mbar_init(uint32_t bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-}
-
-// One bulk copy global -> shared of `bytes` (a multiple of 16, both addresses
-// 16-byte aligned), completing `bytes` transactions on `bar`.
-GRF_DEV void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-      "l"(src), "r"(bytes), "r"(bar)
-      : "memory");
-}
-
-// Wait for the phase of `bar` with the given parity; false after the limits.
-GRF_DEV bool mbar_wait(uint32_t bar, uint32_t parity) {
-  unsigned long long t0 = 0;
-  for (unsigned it = 0; it < kTmaSpinCap; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if ((it & 255) == 0) {
-      const unsigned long long t = tma_clock_ns();
-      if (it == 0) t0 = t;
-      else if (t - t0 > kTmaTimeoutNs) return false;
-    }
-  }
-  return false;
-}
-
-}  // namespace
+using namespace tma;
 
 template <int P>
 __global__ void __launch_bounds__(kMaxThreads<P>, kMinBlocks<P>)

@@ -135,6 +135,31 @@ size_t r2r_smem_bytes(int N, int C);
 int r2r_points_per_thread(int N);
 int r2r_lines_per_cta(int N);  // the default C for lines of N + 1 points
 
+// The 3-D plane path of Algorithm 2 (plane3d.cu).  N2 = R Q.  Pass 1 draws the
+// noise, runs the inverse FFT along axis 1 and the first radix-R step of the
+// axis-2 inverse FFT (decimation in frequency), and writes R independent
+// sub-planes per j1:
+//   ws[field][j1][s][k'][k3] = w^{k' s} sum_r X[j1, k' + Q r, k3] e^{2 pi i r s / R},
+//   w = e^{2 pi i / N2}, k' < Q, k3 <= M (row pitch S3 = M + 2);
+// pass 2 takes one sub-plane per CTA (one bulk copy into shared memory), runs
+// the length-Q inverse FFTs along k' (giving the axis-2 outputs j2 = s + R j'),
+// forms the c2r split and the M-point inverse FFT of every row, and writes each
+// row of N3 = 2M reals with one bulk copy.
+struct PlaneArgs {
+  int N1, N2, M;
+  int R, Q, S3;
+  float2* ws;          // sub-planes of this launch's fields
+  float* out;          // fields [field][j1][j2][N3]
+  const float2* tw;    // tw[L + k] = exp(2 pi i k / L)
+  const float2* tws;   // stage tables (see fft_core)
+  int* status;         // GRF_ERR_TIMEOUT if a bulk copy's wait ran out
+};
+// R for a 3-D plan (1, 2 or 4), or 0 if the plane path does not apply.
+int plane3_radix(int N1, int N2, int M);
+size_t plane3_ws_entries(int N1, int N2, int M);  // per field
+cudaError_t launch_plane3_noise(const ColArgs& a, const PlaneArgs& pl, int64_t nfields, cudaStream_t s);
+cudaError_t launch_plane3_c2r(const PlaneArgs& pl, int64_t nfields, cudaStream_t s);
+
 // Host launchers (fft_kernels.cu).  P is the points per thread of the
 // transform (16 if the length is >= 16, else the length itself).
 cudaError_t launch_col(int src, int mode, int P, const ColArgs& a, dim3 grid, cudaStream_t s);
