@@ -42,8 +42,8 @@ Conventions (the readings of the paper that this oracle fixes):
   Algorithm 2, counter (q_lo, q_hi, 0, 0), M = N_d/2:
     d = 1, entry k_d: call q = k_d >> 1, words 2(k_d & 1) and 2(k_d & 1) + 1;
     d >= 2, entry (k_1, k_mid, k_d) (k_mid = k_2 in 3-D, 0 in 2-D, N_mid = N_2
-    or 1): call q = ((k_1 >> 1) N_mid + k_mid)(M + 1) + k_d, words 2(k_1 & 1)
-    and 2(k_1 & 1) + 1 (rows k_1 = 2i and 2i + 1 share a call).
+    or 1), H = N_1/2: call q = ((k_1 mod H) N_mid + k_mid)(M + 1) + k_d, words
+    2 [k_1 >= H] and 2 [k_1 >= H] + 1 (rows k_1 and k_1 + H share a call).
   Algorithm 1, real grid point with
   flat index j: call q = j >> 2, counter (q_lo, q_hi, 1, 0), pair
   t = (j & 3) >> 1 uses words 2t, 2t+1; the even j takes the cosine normal,
@@ -301,12 +301,13 @@ def alg2_normals(n: Sequence[int], seed: int):
         sel = (kd & np.uint64(1)).astype(bool)
     else:
         nmid = n[1] if d == 3 else 1
+        half = np.uint64(n[0] // 2)
         k1 = np.arange(n[0], dtype=np.uint64).reshape((-1,) + (1,) * (d - 1))
         kmid = np.arange(nmid, dtype=np.uint64).reshape((1, -1, 1)) if d == 3 else np.uint64(0)
         kd = np.arange(M + 1, dtype=np.uint64).reshape((1,) * (d - 1) + (-1,))
-        q = ((k1 >> np.uint64(1)) * np.uint64(nmid) + kmid) * np.uint64(M + 1) + kd
+        q = ((k1 % half) * np.uint64(nmid) + kmid) * np.uint64(M + 1) + kd
         q = np.broadcast_to(q, hs)
-        sel = np.broadcast_to((k1 & np.uint64(1)).astype(bool), hs)
+        sel = np.broadcast_to(k1 >= half, hs)
     w = philox_words(q, TAG_ALG2, seed)
     wa = np.where(sel, w[2], w[0])
     wb = np.where(sel, w[3], w[1])
