@@ -24,9 +24,9 @@
  *     field b, mapped to an exact uniform u = (2 (x >> 9) + 1) 2^-24 and to
  *     normals by Box-Muller; Algorithm 2, counter (q_lo, q_hi, 0, 0): in 1-D
  *     entry k_d uses call k_d >> 1, words 2 (k_d & 1) and 2 (k_d & 1) + 1; in
- *     2-D/3-D entry (k_1, k_mid, k_d) (k_mid = k_2 in 3-D, else 0) uses call
- *     ((k_1 >> 1) N_mid + k_mid)(N_d/2 + 1) + k_d, words 2 (k_1 & 1) and
- *     2 (k_1 & 1) + 1 (N_mid = N_2 in 3-D, else 1); Algorithm 1 point j uses call
+ *     2-D/3-D entry (k_1, k_mid, k_d) (k_mid = k_2 in 3-D, else 0) uses, with
+ *     H = N_1/2, call ((k_1 mod H) N_mid + k_mid)(N_d/2 + 1) + k_d, words
+ *     2 [k_1 >= H] and 2 [k_1 >= H] + 1 (N_mid = N_2 in 3-D, else 1); Algorithm 1 point j uses call
  *     j >> 2, counter (q_lo, q_hi, 1, 0), words 2t, 2t+1 with t = (j & 3) >> 1,
  *     even j taking the cosine normal and odd j the sine normal.
  *
@@ -238,7 +238,7 @@ grf_status grf_rfft_forward(grf_plan p, int64_t batch, const void* in, void* out
 /*
  * grf_batch_plan_create - plan for `count` independent fields of uneven shapes
  * and dimensions, each with its own Matern or Gaussian parameters (FP32,
- * Algorithm 2), sampled together by one persistent kernel.
+ * Algorithm 2), sampled together (see grf_batch_set_mode for the two ways).
  *   d      : host array [count] of dimensions (1..3).
  *   n      : host array [count * 3]; field i uses n[3i .. 3i + d[i] - 1].
  *   L      : host array [count * 3], same indexing.
@@ -251,18 +251,20 @@ grf_status grf_batch_plan_create(grf_plan* out, int64_t count, const int* d, con
                                  const double* L, const grf_spectrum* spec, int prec);
 
 /*
- * grf_batch_sample - sample every field of a batch plan in one persistent
- * launch.  Field i uses Philox key seed + i.
+ * grf_batch_sample - sample every field of a batch plan.  Field i uses
+ * Philox key seed + i.
  *   out : host array [count] of device pointers, out[i] receiving field i
  *         (N_1 x ... x N_d floats).  The pointer array is copied at call time.
- * Waits inside the kernel are bounded; if one runs out the kernel records
- * GRF_ERR_TIMEOUT in the plan's status word and returns.
+ * In the persistent mode, waits inside the kernel are bounded; if one runs
+ * out the kernel records GRF_ERR_TIMEOUT in the plan's status word and returns.
  */
 grf_status grf_batch_sample(grf_plan p, uint64_t seed, void* const* out, void* stream);
 
 /*
  * grf_batch_graph_launch - the same as grf_batch_sample, replayed from a CUDA
- * graph captured on the first call for this (plan, output pointer set).
+ * graph captured for this (plan, mode, output pointer set).  In the per-shape
+ * mode the call that captures the graph samples by direct launches and later
+ * calls replay it; in the persistent mode the first call captures and replays.
  * The seed is read from plan memory at replay, so any seed may be used.
  */
 grf_status grf_batch_graph_launch(grf_plan p, uint64_t seed, void* const* out, void* stream);
@@ -305,6 +307,21 @@ grf_status grf_sample_2d_static(const int64_t* n, const double* L, const grf_spe
  * withhold_field = -1 restores normal operation.  Drops any captured graph.
  */
 grf_status grf_batch_set_debug(grf_plan p, int withhold_field, double timeout_ms);
+
+/*
+ * grf_batch_set_mode - how a batch plan samples (no counterpart in the paper):
+ *   0 (default): per-shape launches.  The fields are grouped by shape; each
+ *     group is sampled by the plan kernels of that shape, one launch index per
+ *     field (its Philox key, s_K table and output looked up by index), and the
+ *     groups run on 8 streams forked from and joined back into `stream`.  No
+ *     kernel waits on another.
+ *   1: one persistent kernel over every (pass, tile) of every field, ordered by
+ *     per-field pass counters with bounded waits.
+ * Both draw the same fields (equal up to FP32 rounding).  A field withheld by
+ * grf_batch_set_debug makes the plan run in mode 1 until it is released.
+ * GRF_ERR_INVALID_ARG for another mode or a plan that is not a batch plan.
+ */
+grf_status grf_batch_set_mode(grf_plan p, int mode);
 
 /*
  * grf_status_word - synchronise `stream`, read and clear the plan's device

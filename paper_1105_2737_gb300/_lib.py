@@ -69,6 +69,7 @@ def lib():
             "grf_batch_graph_launch": (C.c_int, [P, U64, C.POINTER(VP), VP]),
             "grf_status_word": (C.c_int, [P, VP]),
             "grf_batch_set_debug": (C.c_int, [P, C.c_int, C.c_double]),
+            "grf_batch_set_mode": (C.c_int, [P, C.c_int]),
             "grf_philox_words": (C.c_int, [U64, C.c_uint32, U64, I64, VP, VP]),
             "grf_cov_origin": (C.c_int, [P, U64, I64, VP, VP]),
             "grf_sample_2d_static": (C.c_int, [C.POINTER(I64), C.POINTER(D), C.POINTER(grf_spectrum), U64, I64,
@@ -191,6 +192,10 @@ def grf_batch_graph_launch(plan, seed, out_ptrs, stream=0):
 
 def grf_batch_set_debug(plan, withhold_field=-1, timeout_ms=0.0):
     check(lib().grf_batch_set_debug(plan, int(withhold_field), float(timeout_ms)), "grf_batch_set_debug")
+
+
+def grf_batch_set_mode(plan, mode):
+    check(lib().grf_batch_set_mode(plan, int(mode)), "grf_batch_set_mode")
 
 
 def grf_status_word(plan, stream=0) -> int:

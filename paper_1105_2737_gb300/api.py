@@ -239,15 +239,21 @@ def grf_fields(theta: torch.Tensor, plan: GRF, seed: int, batch: int) -> torch.T
 
 
 class GRFBatch:
-    """Uneven batch: fields of different shapes/dimensions/parameters in one persistent launch."""
+    """Uneven batch: fields of different shapes/dimensions/parameters sampled together,
+    by per-shape launches in one graph (mode "shapes", the default) or by one
+    persistent kernel (mode "persistent")."""
 
-    def __init__(self, shapes, lengths, specs, device=None):
+    def __init__(self, shapes, lengths, specs, device=None, mode: str = "shapes"):
         self.shapes = [tuple(int(s) for s in shp) for shp in shapes]
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         spec_objs = [L.make_spectrum(_FAMILIES[s.get("family", "matern")], s.get("sigma", 1.0), s.get("ell", 0.1),
                                      s.get("nu", 1.5)) for s in specs]
         with torch.cuda.device(self.device):
             self.handle = L.grf_batch_plan_create([len(s) for s in self.shapes], self.shapes, lengths, spec_objs)
+        self.set_mode(mode)
+
+    def set_mode(self, mode: str):
+        L.grf_batch_set_mode(self.handle, {"shapes": 0, "persistent": 1}[mode])
 
     def empty(self):
         return [torch.empty(shp, dtype=torch.float32, device=self.device) for shp in self.shapes]

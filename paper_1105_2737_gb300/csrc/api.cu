@@ -1335,6 +1335,14 @@ grf_status grf_batch_set_debug(grf_plan p, int withhold_field, double timeout_ms
   return batch_plan_debug(p->batch, withhold_field, timeout_ms);
 }
 
+grf_status grf_batch_set_mode(grf_plan p, int mode) {
+  grf_status st = check_plan(p);
+  if (st != GRF_OK) return st;
+  if (p->kind != 1) return fail(GRF_ERR_INVALID_ARG, "not a batch plan");
+  if (batch_plan_set_mode(p->batch, mode) != GRF_OK) return fail(GRF_ERR_INVALID_ARG, "batch mode must be 0 or 1");
+  return GRF_OK;
+}
+
 grf_status grf_status_word(grf_plan p, void* stream) {
   grf_status st = check_plan(p);
   if (st != GRF_OK) return st;

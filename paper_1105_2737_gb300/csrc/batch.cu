@@ -31,6 +31,7 @@
 #include <cstring>
 #include <mutex>
 #include <sstream>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -207,6 +208,29 @@ struct BatchPlan {
   BatchParams kparams{};
   int withhold = -1;
   long long timeout_ns = kDefaultTimeoutNs;
+  // Per-shape launches (the default mode): fields grouped by shape, each class
+  // sampled by the plan kernels with one launch index z per field, the classes
+  // spread over several streams; one captured graph replays them all.
+  struct ShapeClass {
+    int d = 1, n[3] = {1, 1, 1};
+    int64_t nf = 0, first = 0;      // fields, offset in the class-ordered arrays
+    int64_t stab_off = 0, fold = 0; // tables: base and stride
+    int64_t ws_off = 0, wstride = 0;
+    int64_t points = 0;
+    int stream = 0;
+  };
+  int mode = 0;  // 0: per-shape launches, 1: one persistent kernel
+  std::vector<ShapeClass> classes;
+  std::vector<int64_t> class_order;  // batch index of each class-ordered slot
+  int64_t* zfield = nullptr;         // device copy of class_order
+  float** zouts = nullptr;           // output pointers, class-ordered
+  uint64_t* seed_dev = nullptr;
+  static constexpr int kStreams = 8;
+  cudaStream_t cstreams[kStreams] = {};
+  cudaEvent_t cfork = nullptr, cjoin[kStreams] = {};
+  cudaGraphExec_t cexec = nullptr;
+  cudaGraph_t cgraph = nullptr;
+  std::vector<void*> cgraph_outs;
 };
 
 namespace {
@@ -451,7 +475,152 @@ cudaError_t set_outs(BatchPlan* b, void* const* out, cudaStream_t s) {
   if (v == b->cur_outs) return cudaSuccess;
   // pageable source: the copy is staged before the call returns, ordered on s
   cudaError_t e = cudaMemcpyAsync(b->outs, v.data(), v.size() * sizeof(void*), cudaMemcpyHostToDevice, s);
+  std::vector<void*> z(b->count);
+  for (int64_t k = 0; k < b->count; ++k) z[k] = v[b->class_order[k]];
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->zouts, z.data(), z.size() * sizeof(void*), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) b->cur_outs = v;
+  return e;
+}
+
+// One shape class: the plan kernels over its nf fields (launch index z =
+// the class-ordered slot first + z), on stream s.
+cudaError_t launch_class(BatchPlan* b, const BatchPlan::ShapeClass& c, cudaStream_t s) {
+  const int d = c.d;
+  const int Nd = c.n[d - 1], M = Nd / 2;
+  const int N1 = d >= 2 ? c.n[0] : 1, Nmid = d == 3 ? c.n[1] : 1;
+  const float2* tws = b->tw + 2 * b->twmax;
+  HalfGeom g{};
+  g.d = d;
+  g.N1 = N1;
+  g.Nmid = Nmid;
+  g.M = M;
+  g.Q = (uint32_t)(M / 2 + 1);
+  g.stab = b->stabs + c.stab_off;
+  g.stab_zstride = c.fold;
+  g.zfield = b->zfield + c.first;
+  g.seed_ptr = b->seed_dev;
+  g.trig = b->tw + 256;
+  float2* ws = b->ws + c.ws_off;
+  float* const* zout = b->zouts + c.first;
+  const int64_t nf = c.nf;
+  cudaError_t e;
+  if (d == 1 && M <= 4096) {
+    RowArgs r{};
+    r.M = M;
+    r.logM = lg2(M);
+    r.C = tile_cols(M, nf, 256);
+    r.rows_per_field = 1;
+    r.nrows = nf;
+    r.T = 1;
+    r.twM = b->tw + M;
+    r.twN = b->tw + Nd;
+    r.tws = tws;
+    r.g = g;
+    r.zout = zout;
+    return launch_row(ROW_NOISE_H, ROW_C2R, 16, r, dim3((unsigned)((nf + r.C - 1) / r.C)), s);
+  }
+  if (d == 1) {
+    const int lm = lg2(M);
+    FourStepArgs fs{};
+    fs.B = 1 << ((lm + 1) / 2);
+    fs.A = M / fs.B;
+    fs.logA = lg2(fs.A);
+    fs.logB = lg2(fs.B);
+    fs.M = M;
+    fs.N = Nd;
+    const int C1 = std::min(4096 / fs.B, fs.A), C2 = std::min(4096 / fs.A, fs.B);
+    fs.T = C1;
+    fs.logT = lg2(C1);
+    fs.Y = ws;
+    fs.Yin = ws;
+    fs.twA = b->tw + fs.A;
+    fs.twB = b->tw + fs.B;
+    fs.twM = b->tw + M;
+    fs.twN = b->tw + Nd;
+    fs.tws = tws;
+    fs.stab = g.stab;
+    fs.stab_zstride = c.fold;
+    fs.trig = g.trig;
+    fs.zfield = g.zfield;
+    fs.seed_ptr = g.seed_ptr;
+    fs.zout = zout;
+    fs.C = C1;
+    if ((e = launch_fourstep(1, 16, fs, nf, s)) != cudaSuccess) return e;
+    fs.C = C2;
+    return launch_fourstep(2, 16, fs, nf, s);
+  }
+  const int T = (d == 2 && N1 >= 256) ? 8 : 1;
+  const int64_t hsize = (int64_t)N1 * Nmid * (M + 1);
+  ColArgs a{};
+  a.N = N1;
+  a.logN = lg2(N1);
+  a.ncols = (int64_t)Nmid * (M + 1);
+  a.T = T;
+  a.logT = lg2(T);
+  a.bstride = hsize;
+  a.out = ws;
+  a.tw = b->tw + N1;
+  a.tws = tws;
+  a.plane_is_k1 = 1;
+  a.g = g;
+  int64_t slots = a.ncols;
+  if (d == 2) {
+    a.zpair = 1;
+    a.twz = b->tw + Nd;
+    slots = M / 2 + 1;
+  }
+  a.C = tile_cols(N1, slots, 256);
+  e = launch_col(COL_NOISE, COL_INV, 16, a, dim3((unsigned)((slots + a.C - 1) / a.C), 1, (unsigned)nf), s);
+  if (e != cudaSuccess) return e;
+  if (d == 3) {
+    ColArgs a2{};
+    a2.N = Nmid;
+    a2.logN = lg2(Nmid);
+    a2.ncols = M + 1;
+    a2.zpair = 1;
+    a2.twz = b->tw + Nd;
+    a2.C = tile_cols(Nmid, M / 2 + 1, 256);
+    a2.T = 1;
+    a2.logT = 0;
+    a2.ostride = (int64_t)Nmid * (M + 1);
+    a2.bstride = hsize;
+    a2.in = ws;
+    a2.out = ws;
+    a2.tw = b->tw + Nmid;
+    a2.tws = tws;
+    a2.g = g;
+    e = launch_col(COL_LOAD, COL_INV, 16, a2, dim3((unsigned)((M / 2 + 1 + a2.C - 1) / a2.C), (unsigned)N1, (unsigned)nf), s);
+    if (e != cudaSuccess) return e;
+  }
+  RowArgs r{};
+  r.M = M;
+  r.logM = lg2(M);
+  r.rows_per_field = (int64_t)N1 * Nmid;
+  r.nrows = nf * r.rows_per_field;
+  r.C = tile_cols(M, r.nrows, 256);
+  r.T = T;
+  r.logT = lg2(T);
+  r.inH = ws;
+  r.twM = b->tw + M;
+  r.twN = b->tw + Nd;
+  r.tws = tws;
+  r.g = g;
+  r.zout = zout;
+  return launch_row(ROW_LOAD_Z, ROW_C2R, 16, r, dim3((unsigned)((r.nrows + r.C - 1) / r.C)), s);
+}
+
+// All classes: forked from s onto the class streams and joined back into s.
+cudaError_t launch_classes(BatchPlan* b, cudaStream_t s) {
+  cudaError_t e = cudaEventRecord(b->cfork, s);
+  for (int q = 0; q < BatchPlan::kStreams && e == cudaSuccess; ++q) e = cudaStreamWaitEvent(b->cstreams[q], b->cfork, 0);
+  for (const auto& c : b->classes) {
+    if (e != cudaSuccess) break;
+    e = launch_class(b, c, b->cstreams[c.stream]);
+  }
+  for (int q = 0; q < BatchPlan::kStreams && e == cudaSuccess; ++q) {
+    e = cudaEventRecord(b->cjoin[q], b->cstreams[q]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->cjoin[q], 0);
+  }
   return e;
 }
 
@@ -569,15 +738,63 @@ grf_status batch_plan_build(BatchPlan** out, int64_t count, const int* d, const 
     }
     hsh = (hsh ^ (uint64_t)(f.d + 7)) * 1099511628211ull;
     f.spec = spec[i];
-    const int M = f.n[f.d - 1] / 2;
-    const int N1 = f.d >= 2 ? f.n[0] : 1, Nmid = f.d == 3 ? f.n[1] : 1;
-    f.stab_off = stab_total;
-    stab_total += (int64_t)(N1 / 2 + 1) * (Nmid / 2 + 1) * (M + 1);
-    stab_total = (stab_total + 63) & ~int64_t(63);
-    f.ws_off = ws_total;
-    ws_total += f.d == 1 ? M : (int64_t)N1 * Nmid * (M + 1);
-    ws_total = (ws_total + 31) & ~int64_t(31);
     b->total_points += f.points;
+  }
+  // shape classes; a class's tables and workspaces are contiguous with a
+  // fixed stride, so that one launch can index them by z
+  {
+    std::vector<int64_t> idx(count);
+    for (int64_t i = 0; i < count; ++i) idx[i] = i;
+    auto key = [&](int64_t i) {
+      const FieldInfo& f = b->fields[i];
+      return std::make_tuple(f.d, f.n[0], f.n[1], f.n[2]);
+    };
+    std::stable_sort(idx.begin(), idx.end(), [&](int64_t x, int64_t y) { return key(x) < key(y); });
+    for (int64_t k = 0; k < count;) {
+      int64_t e = k;
+      while (e < count && key(idx[e]) == key(idx[k])) ++e;
+      BatchPlan::ShapeClass c;
+      const FieldInfo& f0 = b->fields[idx[k]];
+      c.d = f0.d;
+      for (int q = 0; q < 3; ++q) c.n[q] = f0.n[q];
+      c.nf = e - k;
+      const int M = f0.n[f0.d - 1] / 2;
+      const int N1 = f0.d >= 2 ? f0.n[0] : 1, Nmid = f0.d == 3 ? f0.n[1] : 1;
+      c.fold = (int64_t)(N1 / 2 + 1) * (Nmid / 2 + 1) * (M + 1);
+      c.wstride = f0.d == 1 ? M : (int64_t)N1 * Nmid * (M + 1);
+      c.stab_off = stab_total;
+      c.ws_off = ws_total;
+      c.points = f0.points * c.nf;
+      for (int64_t r = k; r < e; ++r) {
+        FieldInfo& f = b->fields[idx[r]];
+        f.stab_off = stab_total + (r - k) * c.fold;
+        f.ws_off = ws_total + (r - k) * c.wstride;
+      }
+      stab_total = (stab_total + c.nf * c.fold + 63) & ~int64_t(63);
+      ws_total = (ws_total + c.nf * c.wstride + 31) & ~int64_t(31);
+      b->classes.push_back(c);
+      k = e;
+    }
+    // the largest classes first, each on the stream with the least work so far
+    std::stable_sort(b->classes.begin(), b->classes.end(),
+                     [](const BatchPlan::ShapeClass& x, const BatchPlan::ShapeClass& y) { return x.points > y.points; });
+    int64_t load[BatchPlan::kStreams] = {};
+    for (auto& c : b->classes) {
+      int best = 0;
+      for (int q = 1; q < BatchPlan::kStreams; ++q)
+        if (load[q] < load[best]) best = q;
+      c.stream = best;
+      load[best] += c.points;
+      c.first = (int64_t)b->class_order.size();
+      // fields of the class in batch order: their offsets are increasing
+      std::vector<int64_t> mem;
+      for (int64_t i = 0; i < count; ++i) {
+        const FieldInfo& f = b->fields[i];
+        if (f.d == c.d && f.n[0] == c.n[0] && f.n[1] == c.n[1] && f.n[2] == c.n[2]) mem.push_back(i);
+      }
+      std::sort(mem.begin(), mem.end(), [&](int64_t x, int64_t y) { return b->fields[x].stab_off < b->fields[y].stab_off; });
+      b->class_order.insert(b->class_order.end(), mem.begin(), mem.end());
+    }
   }
   sig << "|" << std::hex << hsh;
   b->signature = sig.str();
@@ -590,6 +807,16 @@ grf_status batch_plan_build(BatchPlan** out, int64_t count, const int* d, const 
   if (e == cudaSuccess) e = cudaMalloc(&b->ws, (size_t)ws_total * sizeof(float2));
   if (e == cudaSuccess) e = cudaMalloc(&b->counters, (size_t)(3 * count + 2) * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&b->outs, (size_t)count * sizeof(float*));
+  if (e == cudaSuccess) e = cudaMalloc(&b->zouts, (size_t)count * sizeof(float*));
+  if (e == cudaSuccess) e = cudaMalloc(&b->zfield, (size_t)count * sizeof(int64_t));
+  if (e == cudaSuccess) e = cudaMalloc(&b->seed_dev, sizeof(uint64_t));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->zfield, b->class_order.data(), (size_t)count * sizeof(int64_t), cudaMemcpyHostToDevice);
+  for (int q = 0; q < BatchPlan::kStreams && e == cudaSuccess; ++q) {
+    e = cudaStreamCreateWithFlags(&b->cstreams[q], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->cjoin[q], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->cfork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = build_twiddles(b->tw, twmax, 0);
   for (int64_t i = 0; i < count && e == cudaSuccess; ++i) {
     const FieldInfo& f = b->fields[i];
@@ -630,6 +857,59 @@ grf_status batch_plan_build(BatchPlan** out, int64_t count, const int* d, const 
   return GRF_OK;
 }
 
+namespace {
+
+// Per-shape mode: the seed goes to device memory (read by every launch), then
+// the class launches, directly or from the graph captured for this output set.
+grf_status sample_classes(BatchPlan* b, uint64_t seed, cudaStream_t s, bool use_graph, std::string* err) {
+  cudaError_t e = cudaMemcpyAsync(b->seed_dev, &seed, sizeof(uint64_t), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && !use_graph) e = launch_classes(b, s);
+  if (e == cudaSuccess && use_graph) {
+    if (!b->cexec || b->cgraph_outs != b->cur_outs) {
+      // this call's fields come from direct launches (which also set every
+      // kernel's attributes outside the capture); the graph serves later calls
+      e = launch_classes(b, s);
+      if (e != cudaSuccess) {
+        *err = std::string("batch launch: ") + cudaGetErrorString(e);
+        return GRF_ERR_CUDA;
+      }
+      if (b->cexec) cudaGraphExecDestroy(b->cexec);
+      if (b->cgraph) cudaGraphDestroy(b->cgraph);
+      b->cexec = nullptr;
+      b->cgraph = nullptr;
+      cudaStream_t cs;
+      e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the class streams are idle
+      if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        cudaError_t le = launch_classes(b, cs);
+        cudaError_t ce = cudaStreamEndCapture(cs, &b->cgraph);
+        e = le != cudaSuccess ? le : ce;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&b->cexec, b->cgraph, 0);
+      cudaStreamDestroy(cs);
+      if (e != cudaSuccess) {
+        if (b->cexec) cudaGraphExecDestroy(b->cexec);
+        if (b->cgraph) cudaGraphDestroy(b->cgraph);
+        b->cexec = nullptr;
+        b->cgraph = nullptr;
+        *err = std::string("batch graph capture: ") + cudaGetErrorString(e);
+        return GRF_ERR_CUDA;
+      }
+      b->cgraph_outs = b->cur_outs;
+      return GRF_OK;
+    }
+    e = cudaGraphLaunch(b->cexec, s);
+  }
+  if (e != cudaSuccess) {
+    *err = std::string("batch launch: ") + cudaGetErrorString(e);
+    return GRF_ERR_CUDA;
+  }
+  return GRF_OK;
+}
+
+}  // namespace
+
 grf_status batch_plan_sample(BatchPlan* b, uint64_t seed, void* const* out, cudaStream_t s, int* status,
                              bool use_graph, std::string* err) {
   for (int64_t i = 0; i < b->count; ++i)
@@ -638,6 +918,11 @@ grf_status batch_plan_sample(BatchPlan* b, uint64_t seed, void* const* out, cuda
       return GRF_ERR_INVALID_ARG;
     }
   cudaError_t e = set_outs(b, out, s);
+  if (e != cudaSuccess) {
+    *err = std::string("batch sample: ") + cudaGetErrorString(e);
+    return GRF_ERR_CUDA;
+  }
+  if (b->mode == 0 && b->withhold < 0) return sample_classes(b, seed, s, use_graph, err);
   if (e == cudaSuccess && !b->tuned) {
     const char* env = std::getenv("GRF_TUNE");
     if (!(env && env[0] == '0')) e = tune(b, seed, s, status);
@@ -718,9 +1003,27 @@ grf_status batch_plan_debug(BatchPlan* b, int withhold_field, double timeout_ms)
 
 int64_t batch_plan_total_points(const BatchPlan* b) { return b ? b->total_points : 0; }
 
+grf_status batch_plan_set_mode(BatchPlan* b, int mode) {
+  if (mode != 0 && mode != 1) return GRF_ERR_INVALID_ARG;
+  b->mode = mode;
+  return GRF_OK;
+}
+
+int batch_plan_mode(const BatchPlan* b) { return b ? b->mode : -1; }
+
 void batch_plan_free(BatchPlan* b) {
   if (!b) return;
   drop_graph(b);
+  if (b->cexec) cudaGraphExecDestroy(b->cexec);
+  if (b->cgraph) cudaGraphDestroy(b->cgraph);
+  for (int q = 0; q < BatchPlan::kStreams; ++q) {
+    if (b->cstreams[q]) cudaStreamDestroy(b->cstreams[q]);
+    if (b->cjoin[q]) cudaEventDestroy(b->cjoin[q]);
+  }
+  if (b->cfork) cudaEventDestroy(b->cfork);
+  cudaFree(b->zouts);
+  cudaFree(b->zfield);
+  cudaFree(b->seed_dev);
   cudaFree(b->tw);
   cudaFree(b->stabs);
   cudaFree(b->ws);

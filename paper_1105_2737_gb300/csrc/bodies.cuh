@@ -32,6 +32,15 @@ GRF_DEV int fold_index(int k1, int kmid, int kd, const HalfGeom& g) {
   return (kd * (g.Nmid / 2 + 1) + fm) * (g.N1 / 2 + 1) + f1;
 }
 
+// The Philox key and the s_K table of the field at launch index z (a batch
+// plan's launch maps z to its batch index and table; a plan's launch takes
+// fields field0 + z with one table).
+GRF_DEV uint64_t field_key(const HalfGeom& g, int64_t z) {
+  const uint64_t seed = g.seed_ptr ? *g.seed_ptr : g.seed;
+  return seed + (uint64_t)(g.zfield ? g.zfield[z] : g.field0 + z);
+}
+GRF_DEV const float* field_stab(const HalfGeom& g, int64_t z) { return g.stab + z * g.stab_zstride; }
+
 // xi_K at (k1, kmid, kd) of field `field`.
 GRF_DEV float2 xi_at(int k1, int kmid, int kd, int64_t field, const HalfGeom& g) {
   return alg2_xi_grid(k1, kmid, kd, g.N1, g.Nmid, g.M, g.seed + (uint64_t)(g.field0 + field), g.trig);
@@ -76,71 +85,27 @@ static __device__ __noinline__ float2 plane_xi(int k1, int kmid, int kd, int N1,
   const int nk1 = (N1 - k1) & (N1 - 1), nkm = (Nmid - kmid) & (Nmid - 1);
   const int row = k1 * Nmid + kmid, nrow = nk1 * Nmid + nkm;
   const bool own = row >= nrow;
-  const float2 z = alg2_normals_grid(own ? k1 : nk1, own ? kmid : nkm, kd, Nmid, M, key, trig);
+  const float2 z = alg2_normals_grid(own ? k1 : nk1, own ? kmid : nkm, kd, N1, Nmid, M, key, trig);
   if (row == nrow) return make_float2(z.x, 0.f);
   const float r2 = 0.70710678118654752440f;
   return make_float2(z.x * r2, own ? z.y * r2 : -z.y * r2);
 }
 
 // Normals (z_re, z_im) of Algorithm 2 for the entries (k1 = tau + TPT q, kmid, kd)
-// of this thread.  Rows k1 = 2i and 2i + 1 share one Philox call (words 0,1 and
-// 2,3).  Three ways to deal the words out, by the thread layout:
-//   NV_INTHREAD (TPT == 1): both rows of a call are this thread's (q and q ^ 1);
-//   NV_SHFL (TPT even, C < 32): they sit on threads tau and tau ^ 1 (lanes t and
-//     t ^ C); each lane draws the call for half of its rows and passes the
-//     partner its words;
-//   NV_PLAIN: every entry draws its own call (lanes t and t ^ C in other warps).
-// NV_ANY picks one at run time; the per-pass kernels are compiled for one
-// variant each, so that the code of the others does not crowd their registers.
+// of this thread (TPT P = N1).  Rows k1 and k1 + N1/2 share one Philox call
+// (words 0,1 and 2,3), and they are this thread's entries q and q + P/2: each
+// call feeds two of the thread's own entries, whatever the layout.
 template <int P>
-GRF_DEV void normals_inthread(float2 (&v)[P], int kmid, int kd, const HalfGeom& g, uint64_t key) {
+GRF_DEV void alg2_column_normals(float2 (&v)[P], int tau, int TPT, int kmid, int kd, const HalfGeom& g,
+                                 uint64_t key) {
+  // row k1 = tau + TPT i (i < P/2) lies below N1/2: its call is (k1 Nmid + kmid)(M + 1) + kd
+  const uint64_t stride = (uint64_t)TPT * (uint64_t)g.Nmid * (uint64_t)(g.M + 1);
+  uint64_t call = ((uint64_t)tau * (uint64_t)g.Nmid + (uint64_t)kmid) * (uint64_t)(g.M + 1) + (uint64_t)kd;
 #pragma unroll
-  for (int i = 0; i < P / 2; ++i) {
-    const u32x4 w = philox_call(alg2_call_index(2 * i, kmid, kd, g.Nmid, g.M), 0u, key);
-    v[2 * i] = box_muller(w.x, w.y, g.trig);
-    v[2 * i + 1] = box_muller(w.z, w.w, g.trig);
-  }
-}
-template <int P>
-GRF_DEV void normals_shfl(float2 (&v)[P], int tau, int TPT, int C, int kmid, int kd, const HalfGeom& g,
-                          uint64_t key) {
-  const bool odd = (tau & 1) != 0;
-  // row k1 = tau + TPT qa has call ((k1 >> 1) Nmid + kmid)(M + 1) + kd; with TPT
-  // even, k1 >> 1 = (tau >> 1) + (TPT / 2) qa, so the calls step by a constant
-  const uint64_t stride = (uint64_t)(TPT >> 1) * (uint64_t)g.Nmid * (uint64_t)(g.M + 1);
-  uint64_t call = alg2_call_index(tau + (odd ? TPT * (P / 2) : 0), kmid, kd, g.Nmid, g.M);
-#pragma unroll
-  for (int i = 0; i < P / 2; ++i, call += stride) {  // this lane draws the call of its row qa
+  for (int i = 0; i < P / 2; ++i, call += stride) {
     const u32x4 w = philox_call(call, 0u, key);
-    const uint32_t oa = odd ? w.z : w.x, ob = odd ? w.w : w.y;
-    const uint32_t pa = odd ? w.x : w.z, pb = odd ? w.y : w.w;
-    const uint32_t ra = __shfl_xor_sync(0xffffffffu, pa, C);
-    const uint32_t rb = __shfl_xor_sync(0xffffffffu, pb, C);
-    const float2 zo = box_muller(oa, ob, g.trig);  // own row qa
-    const float2 zr = box_muller(ra, rb, g.trig);  // own row qb, drawn by the partner
-    v[i] = odd ? zr : zo;
-    v[i + P / 2] = odd ? zo : zr;
-  }
-}
-template <int P>
-GRF_DEV void normals_plain(float2 (&v)[P], int tau, int TPT, int kmid, int kd, const HalfGeom& g, uint64_t key) {
-#pragma unroll
-  for (int q = 0; q < P; ++q) v[q] = alg2_normals_grid(tau + TPT * q, kmid, kd, g.Nmid, g.M, key, g.trig);
-}
-
-template <int P, int NV = NV_ANY>
-GRF_DEV void alg2_column_normals(float2 (&v)[P], int tau, int TPT, int C, int kmid, int kd,
-                                 const HalfGeom& g, uint64_t key) {
-  if constexpr (NV == NV_INTHREAD) {
-    normals_inthread<P>(v, kmid, kd, g, key);
-  } else if constexpr (NV == NV_SHFL) {
-    normals_shfl<P>(v, tau, TPT, C, kmid, kd, g, key);
-  } else if constexpr (NV == NV_PLAIN) {
-    normals_plain<P>(v, tau, TPT, kmid, kd, g, key);
-  } else {
-    if (TPT == 1) normals_inthread<P>(v, kmid, kd, g, key);
-    else if (C < 32) normals_shfl<P>(v, tau, TPT, C, kmid, kd, g, key);
-    else normals_plain<P>(v, tau, TPT, kmid, kd, g, key);
+    v[i] = box_muller(w.x, w.y, g.trig);
+    v[i + P / 2] = box_muller(w.z, w.w, g.trig);
   }
 }
 
@@ -157,7 +122,7 @@ GRF_DEV int64_t col_offset(const ColArgs& a, int pos, int col) {
 // pos = tau + TPT q.  `base` is the offset of the column's plane and field.
 // LN, CC: a compile-time transform length 2^LN and CC columns per CTA (see
 // pass_kernels.cuh); 0 takes them from the launch descriptor.
-template <int P, int SRC, int MODE, int NV = NV_ANY, int LN = 0>
+template <int P, int SRC, int MODE, int LN = 0>
 GRF_DEV void col_transform(const ColArgs& a, int col, bool valid, int64_t field, int64_t base, int tau, int c,
                            int C, int nthr, float2* sm, float2 (&v)[P], ColGeom& cg) {
   const int N = LN ? (1 << LN) : a.N;
@@ -168,10 +133,11 @@ GRF_DEV void col_transform(const ColArgs& a, int col, bool valid, int64_t field,
 
   if constexpr (SRC == COL_NOISE) {
     const HalfGeom& g = a.g;
-    const uint64_t key = g.seed + (uint64_t)(g.field0 + field);
+    const uint64_t key = field_key(g, field);
     // s_K of this column: the folded table row (kd, fmid) is contiguous along axis 1
-    const float* srow = g.stab + (cg.kd * (g.Nmid / 2 + 1) + min(cg.kmid, g.Nmid - cg.kmid)) * (g.N1 / 2 + 1);
-    alg2_column_normals<P, NV>(v, tau, TPT, C, cg.kmid, cg.kd, g, key);
+    const float* srow =
+        field_stab(g, field) + (cg.kd * (g.Nmid / 2 + 1) + min(cg.kmid, g.Nmid - cg.kmid)) * (g.N1 / 2 + 1);
+    alg2_column_normals<P>(v, tau, TPT, cg.kmid, cg.kd, g, key);
     // s_K read after the normals: the loads do not hold registers during the draw
     float s[P];
 #pragma unroll
@@ -269,7 +235,7 @@ GRF_DEV PairIdx pair_idx(const ColArgs& a, const Coords& co) {
   return r;
 }
 
-template <int P, int SRC, int MODE, int NV = NV_ANY, int LN = 0, int CC = 0, class Coords>
+template <int P, int SRC, int MODE, int LN = 0, int CC = 0, class Coords>
 GRF_DEV void col_body_pair(const ColArgs& a, const Coords& co, int nthr_rt, float2* sm) {
   static_assert(MODE == COL_INV || MODE == COL_FWD_SCALE_INV, "pair mode ends an inverse pass");
   const int N = LN ? (1 << LN) : a.N;
@@ -303,7 +269,7 @@ GRF_DEV void col_body_pair(const ColArgs& a, const Coords& co, int nthr_rt, floa
   } else {
     {
       const PairIdx x = pair_idx<CC>(a, co);
-      col_transform<P, SRC, MODE, NV, LN>(a, x.ca, x.valid, x.field, x.base, x.tau, x.c, C, nthr, sm, v, cg);
+      col_transform<P, SRC, MODE, LN>(a, x.ca, x.valid, x.field, x.base, x.tau, x.c, C, nthr, sm, v, cg);
     }
     float2* stash = sm + (size_t)spad(N) * C + co.tid();
 #pragma unroll
@@ -312,7 +278,7 @@ GRF_DEV void col_body_pair(const ColArgs& a, const Coords& co, int nthr_rt, floa
       // pair M/2 is one column: its second transform only keeps the CTA's
       // barriers in step (an in-place pass has already replaced its input)
       const PairIdx x = pair_idx<CC>(a, co);
-      col_transform<P, SRC, MODE, NV, LN>(a, x.cb, x.valid && x.ca != x.cb, x.field, x.base, x.tau, x.c, C, nthr,
+      col_transform<P, SRC, MODE, LN>(a, x.cb, x.valid && x.ca != x.cb, x.field, x.base, x.tau, x.c, C, nthr,
                                           sm, v, cg);
     }
   }
@@ -336,7 +302,7 @@ GRF_DEV void col_body_pair(const ColArgs& a, const Coords& co, int nthr_rt, floa
 
 // One CTA: C columns of plane `by` of field `bz`, X stored (or, for the
 // adjoint, reduced).
-template <int P, int SRC, int MODE, int NV = NV_ANY, int LN = 0, int CC = 0>
+template <int P, int SRC, int MODE, int LN = 0, int CC = 0>
 GRF_DEV void col_body(const ColArgs& a, int bx, int by, int64_t bz, int64_t blk, int nthr_rt, float2* sm) {
   const int C = CC ? CC : a.C;
   const int nthr = (LN && CC) ? CC * (1 << LN) / P : nthr_rt;
@@ -351,7 +317,7 @@ GRF_DEV void col_body(const ColArgs& a, int bx, int by, int64_t bz, int64_t blk,
 
   const int col = bx * C + c;
   const bool valid = col < a.ncols;
-  col_transform<P, SRC, MODE, NV, LN>(a, col, valid, field, base, tau, c, C, nthr, sm, v, cg);
+  col_transform<P, SRC, MODE, LN>(a, col, valid, field, base, tau, c, C, nthr, sm, v, cg);
 
   if constexpr (MODE == COL_FWD_ADJ) {
     // v[q] = G^ at K = (k1, kmid, kd).  Sum w_K d_theta s_K Re(xi_K conj G^_K).
@@ -411,7 +377,9 @@ GRF_DEV float2 r2c_post(float2 Zk, float2 Zmk, float2 w) {
 
 // LN, CC: a compile-time length M = 2^LN and CC rows per CTA (see
 // pass_kernels.cuh); 0 takes them from the launch descriptor.
-template <int P, int SRC, int MODE, int LN = 0, int CC = 0, int TT = 0>
+// BZ: the output pointer comes from a.zout (1, a batch plan's launch), from
+// a.outR (0), or whichever is set (-1).
+template <int P, int SRC, int MODE, int LN = 0, int CC = 0, int TT = 0, int BZ = -1>
 GRF_DEV void row_body(const RowArgs& a, int64_t bx, int nthr_rt, float2* sm) {
   const int C = CC ? CC : a.C;
   const int nthr = (LN && CC) ? CC * (1 << LN) / P : nthr_rt;
@@ -439,7 +407,10 @@ GRF_DEV void row_body(const RowArgs& a, int64_t bx, int nthr_rt, float2* sm) {
       v[q] = valid ? __ldcg(src + ((int64_t)(tau + TPT * q) << logT)) : make_float2(0.f, 0.f);
     fft_core<P, +1>(v, sm, tau, c, C, M, logM, a.twM, a.tws, nthr);
     if (valid) {
-      float2* o = reinterpret_cast<float2*>(a.outR + g * N);
+      // (the row's field is formed only for a batch plan's launch)
+      const bool bz = BZ < 0 ? a.zout != nullptr : BZ == 1;
+      float2* o = reinterpret_cast<float2*>(
+          bz ? a.zout[g / a.rows_per_field] + (g % a.rows_per_field) * N : a.outR + g * N);
 #pragma unroll
       for (int q = 0; q < P; ++q) o[tau + TPT * q] = v[q];
     }
@@ -447,15 +418,16 @@ GRF_DEV void row_body(const RowArgs& a, int64_t bx, int nthr_rt, float2* sm) {
   } else if constexpr (MODE == ROW_C2R) {
     // ROW_NOISE_H (d = 1, one row per field): stage X[0..M] of every row of
     // the CTA in shared memory, then split into Z.
-    const uint64_t key = a.g.seed + (uint64_t)(a.g.field0 + field);
+    const uint64_t key = field_key(a.g, field);
+    const float* stab = field_stab(a.g, field);
     float2 xm = make_float2(0.f, 0.f);
     if (valid) {
 #pragma unroll
       for (int q = 0; q < P; ++q) {
         const int k = tau + TPT * q;
-        v[q] = cscale(alg2_xi_1d(k, M, key, a.g.trig), __ldg(a.g.stab + k));
+        v[q] = cscale(alg2_xi_1d(k, M, key, a.g.trig), __ldg(stab + k));
       }
-      if (tau == 0) xm = cscale(alg2_xi_1d(M, M, key, a.g.trig), __ldg(a.g.stab + M));
+      if (tau == 0) xm = cscale(alg2_xi_1d(M, M, key, a.g.trig), __ldg(stab + M));
     } else {
 #pragma unroll
       for (int q = 0; q < P; ++q) v[q] = make_float2(0.f, 0.f);
@@ -472,7 +444,7 @@ GRF_DEV void row_body(const RowArgs& a, int64_t bx, int nthr_rt, float2* sm) {
     if constexpr (P < 16) cta_sync(nthr);
     fft_core<P, +1>(v, sm, tau, c, C, M, logM, a.twM, a.tws, nthr);
     if (valid) {
-      float2* o = reinterpret_cast<float2*>(a.outR + g * N);
+      float2* o = reinterpret_cast<float2*>(a.zout ? a.zout[field] + rowf * N : a.outR + g * N);
 #pragma unroll
       for (int q = 0; q < P; ++q) o[tau + TPT * q] = v[q];
     }
@@ -605,13 +577,14 @@ GRF_DEV void fourstep1_body(const FourStepArgs& a, int bx, int64_t bz, int nthr,
   const int TPT = a.B / P;
   const int k1 = bx * C + c;  // < A: C divides A
   const int64_t field = bz;
-  const uint64_t key = a.seed + (uint64_t)(a.field0 + field);
+  const uint64_t key = (a.seed_ptr ? *a.seed_ptr : a.seed) + (uint64_t)(a.zfield ? a.zfield[field] : a.field0 + field);
+  const float* stab = a.stab + field * a.stab_zstride;
   float2 v[P];
 #pragma unroll
   for (int q = 0; q < P; ++q) {
     const int k = k1 + a.A * (tau + TPT * q);
     const int mk = a.M - k;  // k = 0 pairs with X[M]
-    v[q] = c2r_pre(x1d(k, a.M, a.stab, key, a.trig), x1d(mk, a.M, a.stab, key, a.trig), __ldg(a.twN + k));
+    v[q] = c2r_pre(x1d(k, a.M, stab, key, a.trig), x1d(mk, a.M, stab, key, a.trig), __ldg(a.twN + k));
   }
   fft_core<P, +1>(v, sm, tau, c, C, a.B, a.logB, a.twB, a.tws, nthr);
   float2* Y = a.Y + field * (int64_t)a.M + ((k1 >> a.logT) * (int64_t)a.B << a.logT) + (k1 & (a.T - 1));
@@ -639,7 +612,7 @@ GRF_DEV void fourstep2_body(const FourStepArgs& a, int bx, int64_t bz, int nthr,
     v[q] = __ldcg(Y + ((k1 >> a.logT) * (int64_t)a.B << a.logT) + (k1 & (a.T - 1)));
   }
   fft_core<P, +1>(v, sm, tau, c, C, a.A, a.logA, a.twA, a.tws, nthr);
-  float2* o = reinterpret_cast<float2*>(a.out + field * (int64_t)a.N);
+  float2* o = reinterpret_cast<float2*>(a.zout ? a.zout[field] : a.out + field * (int64_t)a.N);
 #pragma unroll
   for (int q = 0; q < P; ++q) o[n2 + (int64_t)a.B * (tau + TPT * q)] = v[q];
 }

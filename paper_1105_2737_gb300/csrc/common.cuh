@@ -117,18 +117,22 @@ GRF_DEV double2 box_muller_d(uint32_t wa, uint32_t wb) {
 }
 
 // Algorithm 2 noise.  1-D: entry kd uses call kd >> 1, words 2 (kd & 1), 2 (kd & 1) + 1.
-// 2-D / 3-D: entry (k1, kmid, kd) uses call ((k1 >> 1) Nmid + kmid)(M + 1) + kd,
-// words 2 (k1 & 1), 2 (k1 & 1) + 1 (rows 2i and 2i + 1 share a call).
-GRF_DEV uint64_t alg2_call_index(int k1, int kmid, int kd, int Nmid, int M) {
-  return ((uint64_t)(k1 >> 1) * (uint64_t)Nmid + (uint64_t)kmid) * (uint64_t)(M + 1) + (uint64_t)kd;
+// 2-D / 3-D: with H = N1 / 2, entry (k1, kmid, kd) uses call
+// ((k1 mod H) Nmid + kmid)(M + 1) + kd, words 2 [k1 >= H], 2 [k1 >= H] + 1
+// (rows k1 and k1 + H share a call).
+GRF_DEV uint64_t alg2_call_index(int k1, int kmid, int kd, int N1, int Nmid, int M) {
+  const int H = N1 >> 1;
+  const int r = k1 >= H ? k1 - H : k1;
+  return ((uint64_t)r * (uint64_t)Nmid + (uint64_t)kmid) * (uint64_t)(M + 1) + (uint64_t)kd;
 }
-GRF_DEV float2 alg2_normals_grid(int k1, int kmid, int kd, int Nmid, int M, uint64_t key, const float2* trig) {
-  const u32x4 w = philox_call(alg2_call_index(k1, kmid, kd, Nmid, M), 0u, key);
-  return (k1 & 1) ? box_muller(w.z, w.w, trig) : box_muller(w.x, w.y, trig);
+GRF_DEV float2 alg2_normals_grid(int k1, int kmid, int kd, int N1, int Nmid, int M, uint64_t key,
+                                 const float2* trig) {
+  const u32x4 w = philox_call(alg2_call_index(k1, kmid, kd, N1, Nmid, M), 0u, key);
+  return k1 >= (N1 >> 1) ? box_muller(w.z, w.w, trig) : box_muller(w.x, w.y, trig);
 }
-GRF_DEV double2 alg2_normals_grid_d(int k1, int kmid, int kd, int Nmid, int M, uint64_t key) {
-  const u32x4 w = philox_call(alg2_call_index(k1, kmid, kd, Nmid, M), 0u, key);
-  return (k1 & 1) ? box_muller_d(w.z, w.w) : box_muller_d(w.x, w.y);
+GRF_DEV double2 alg2_normals_grid_d(int k1, int kmid, int kd, int N1, int Nmid, int M, uint64_t key) {
+  const u32x4 w = philox_call(alg2_call_index(k1, kmid, kd, N1, Nmid, M), 0u, key);
+  return k1 >= (N1 >> 1) ? box_muller_d(w.z, w.w) : box_muller_d(w.x, w.y);
 }
 GRF_DEV float2 alg2_normals_1d(int kd, uint64_t key, const float2* trig) {
   const u32x4 w = philox_call((uint64_t)(kd >> 1), 0u, key);
@@ -143,34 +147,34 @@ GRF_DEV float2 alg2_xi_grid(int k1, int kmid, int kd, int N1, int Nmid, int M, u
                             const float2* trig) {
   const float r2 = 0.70710678118654752440f;
   if (kd != 0 && kd != M) {
-    const float2 z = alg2_normals_grid(k1, kmid, kd, Nmid, M, key, trig);
+    const float2 z = alg2_normals_grid(k1, kmid, kd, N1, Nmid, M, key, trig);
     return make_float2(z.x * r2, z.y * r2);
   }
   const int nk1 = k1 ? N1 - k1 : 0, nkm = kmid ? Nmid - kmid : 0;  // -K mod N for any even N
   const int row = k1 * Nmid + kmid, nrow = nk1 * Nmid + nkm;
-  if (row == nrow) return make_float2(alg2_normals_grid(k1, kmid, kd, Nmid, M, key, trig).x, 0.0f);
+  if (row == nrow) return make_float2(alg2_normals_grid(k1, kmid, kd, N1, Nmid, M, key, trig).x, 0.0f);
   if (row > nrow) {
-    const float2 z = alg2_normals_grid(k1, kmid, kd, Nmid, M, key, trig);
+    const float2 z = alg2_normals_grid(k1, kmid, kd, N1, Nmid, M, key, trig);
     return make_float2(z.x * r2, z.y * r2);
   }
-  const float2 z = alg2_normals_grid(nk1, nkm, kd, Nmid, M, key, trig);
+  const float2 z = alg2_normals_grid(nk1, nkm, kd, N1, Nmid, M, key, trig);
   return make_float2(z.x * r2, -z.y * r2);
 }
 GRF_DEV double2 alg2_xi_grid_d(int k1, int kmid, int kd, int N1, int Nmid, int M, uint64_t key) {
   const double r2 = 0.70710678118654752440;
   if (kd != 0 && kd != M) {
-    const double2 z = alg2_normals_grid_d(k1, kmid, kd, Nmid, M, key);
+    const double2 z = alg2_normals_grid_d(k1, kmid, kd, N1, Nmid, M, key);
     return make_double2(z.x * r2, z.y * r2);
   }
   // -K mod N for any even N (the FP64 form also takes sizes that are not powers of two)
   const int nk1 = k1 ? N1 - k1 : 0, nkm = kmid ? Nmid - kmid : 0;
   const int row = k1 * Nmid + kmid, nrow = nk1 * Nmid + nkm;
-  if (row == nrow) return make_double2(alg2_normals_grid_d(k1, kmid, kd, Nmid, M, key).x, 0.0);
+  if (row == nrow) return make_double2(alg2_normals_grid_d(k1, kmid, kd, N1, Nmid, M, key).x, 0.0);
   if (row > nrow) {
-    const double2 z = alg2_normals_grid_d(k1, kmid, kd, Nmid, M, key);
+    const double2 z = alg2_normals_grid_d(k1, kmid, kd, N1, Nmid, M, key);
     return make_double2(z.x * r2, z.y * r2);
   }
-  const double2 z = alg2_normals_grid_d(nk1, nkm, kd, Nmid, M, key);
+  const double2 z = alg2_normals_grid_d(nk1, nkm, kd, N1, Nmid, M, key);
   return make_double2(z.x * r2, -z.y * r2);
 }
 // 1-D: the self-conjugate points are kd = 0 and kd = M; everything else is generic.

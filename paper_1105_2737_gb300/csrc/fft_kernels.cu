@@ -90,10 +90,10 @@ cudaError_t prepare_kernel(const void* k, int threads, size_t smem) {
 template <int SRC, int MODE, int PAIR = 0>
 static cudaError_t launch_col_p(int P, const ColArgs& a, dim3 grid, cudaStream_t s) {
   switch (P) {
-    case 2: return launch_col_t<2, SRC, MODE, PAIR, NV_ANY>(a, grid, s);
-    case 4: return launch_col_t<4, SRC, MODE, PAIR, NV_ANY>(a, grid, s);
-    case 8: return launch_col_t<8, SRC, MODE, PAIR, NV_ANY>(a, grid, s);
-    case 16: return launch_col_t<16, SRC, MODE, PAIR, NV_ANY>(a, grid, s);
+    case 2: return launch_col_t<2, SRC, MODE, PAIR>(a, grid, s);
+    case 4: return launch_col_t<4, SRC, MODE, PAIR>(a, grid, s);
+    case 8: return launch_col_t<8, SRC, MODE, PAIR>(a, grid, s);
+    case 16: return launch_col_t<16, SRC, MODE, PAIR>(a, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }

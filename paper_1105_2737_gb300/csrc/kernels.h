@@ -14,9 +14,6 @@ enum ColMode {
   COL_FWD_ADJ = 3         // forward, then reduce against regenerated xi (adjoint)
 };
 
-// How the noise pass deals Philox words to threads (see alg2_column_normals).
-enum NoiseVariant { NV_SHFL = 0, NV_INTHREAD = 1, NV_PLAIN = 2, NV_ANY = 3 };
-inline int noise_variant(int N, int P, int C) { return N == P ? NV_INTHREAD : (C < 32 ? NV_SHFL : NV_PLAIN); }
 
 // Sources and modes of the row pass (the contiguous last axis).
 //   ROW_LOAD_Z: Z[k] = (X[k] + conj X[M-k]) + i e^{2 pi i k/N} (X[k] - conj X[M-k]),
@@ -43,6 +40,13 @@ struct HalfGeom {
   float inv_sigma;        // d s_K / d sigma = s_K / sigma, adjoint only
   const float2* trig;     // exp(2 pi i h / 256), h < 256: coarse angles of Box-Muller
   float alg1_scale;       // 1 / sqrt(N_tot), Algorithm 1
+  // Launches over fields of a batch plan (NULL / 0 otherwise): the batch index
+  // of the field at launch index z (the key is seed + zfield[z]), the stride
+  // between the fields' s_K tables, and the seed read from device memory (so
+  // that a captured graph takes any seed).
+  const int64_t* zfield;
+  int64_t stab_zstride;
+  const uint64_t* seed_ptr;
 };
 
 struct ColArgs {
@@ -79,6 +83,7 @@ struct RowArgs {
   const float2* tws;  // radix-16 stage tables (see fft_core)
   HalfGeom g;
   double* partial;    // ROW_R2C_ADJ
+  float* const* zout; // batch plans: output of the field at launch index z (NULL: outR + z field size)
 };
 
 // Four-step c2r for long 1-D grids (Algorithm 2): M = N/2 = A * B.
@@ -104,6 +109,11 @@ struct FourStepArgs {
   const float2* trig;  // exp(2 pi i h / 256)
   uint64_t seed;
   int64_t field0;
+  // batch plans (NULL / 0 otherwise), as in HalfGeom and RowArgs
+  const int64_t* zfield;
+  int64_t stab_zstride;
+  const uint64_t* seed_ptr;
+  float* const* zout;
 };
 cudaError_t launch_fourstep(int stage, int P, const FourStepArgs& a, int64_t nfields, cudaStream_t s);
 

@@ -39,7 +39,7 @@ bool launch_noise_pair_fast(int P, const ColArgs& a, dim3 grid, cudaStream_t s, 
   if (!a.zpair || !a.plane_is_k1 || a.g.d != 2 || a.g.Nmid != 1 || grid.y != 1) return false;
   if ((int64_t)a.N * (a.g.M + 1) >= (int64_t(1) << 31)) return false;
   const int ln = spec_ln(P, a.N, a.C, 256, 4096);
-  if (!ln || noise_variant(a.N, P, a.C) != NV_SHFL) return false;
+  if (!ln) return false;
   switch (ln) {
     case 8: return fast_ln<8>(a, grid, s, err);
     case 9: return fast_ln<9>(a, grid, s, err);

@@ -2,7 +2,7 @@
 // the c2r split Z), specialised for the 256-thread radix-16 geometries:
 // transform length N = 2^LN (256..4096), CC = 4096 / N column pairs per CTA,
 // workspace tile T = TT.  Same arithmetic and same outputs as col_body_pair
-// with SRC = COL_NOISE, MODE = COL_INV, NV = NV_SHFL (bit for bit up to the
+// with SRC = COL_NOISE, MODE = COL_INV (bit for bit up to the
 // rounding of the Box-Muller scale, see box_muller_half), with fewer
 // instructions per entry:
 //   - the field's Philox key is formed from the block index (uniform across
@@ -40,25 +40,19 @@ GRF_DEV float2 box_muller_half(uint32_t wa, uint32_t wb, const float2* strig) {
 }
 
 // Interior-column normals (z_re + i z_im) / sqrt 2 of the entries
-// k1 = tau + TPT q of column kd (2-D: call (k1 >> 1)(M + 1) + kd, words
-// 2 (k1 & 1), +1), the rows 2i and 2i + 1 of a call sitting on lanes t and
-// t ^ CC (the NV_SHFL way of dealing the words).
-template <int P, int TPT, int CC>
-GRF_DEV void normals_half_shfl(float2 (&v)[P], int tau, int kd, int M, uint64_t key, const float2* strig) {
-  const bool odd = (tau & 1) != 0;
-  const uint64_t stride = (uint64_t)(TPT >> 1) * (uint64_t)(M + 1);
-  uint64_t call = (uint64_t)((tau + (odd ? TPT * (P / 2) : 0)) >> 1) * (uint64_t)(M + 1) + (uint64_t)kd;
+// k1 = tau + TPT q of column (kmid, kd) (call ((k1 mod N1/2) Nmid + kmid)(M + 1)
+// + kd, words 2 [k1 >= N1/2], +1): the rows k1 and k1 + N1/2 of a call are this
+// thread's entries q and q + P/2.
+template <int P, int TPT>
+GRF_DEV void normals_half(float2 (&v)[P], int tau, int kmid, int kd, int Nmid, int M, uint64_t key,
+                          const float2* strig) {
+  const uint64_t stride = (uint64_t)TPT * (uint64_t)Nmid * (uint64_t)(M + 1);
+  uint64_t call = ((uint64_t)tau * (uint64_t)Nmid + (uint64_t)kmid) * (uint64_t)(M + 1) + (uint64_t)kd;
 #pragma unroll
   for (int i = 0; i < P / 2; ++i, call += stride) {
     const u32x4 w = philox_call(call, 0u, key);
-    const uint32_t oa = odd ? w.z : w.x, ob = odd ? w.w : w.y;
-    const uint32_t pa = odd ? w.x : w.z, pb = odd ? w.y : w.w;
-    const uint32_t ra = __shfl_xor_sync(0xffffffffu, pa, CC);
-    const uint32_t rb = __shfl_xor_sync(0xffffffffu, pb, CC);
-    const float2 zo = box_muller_half(oa, ob, strig);
-    const float2 zr = box_muller_half(ra, rb, strig);
-    v[i] = odd ? zr : zo;
-    v[i + P / 2] = odd ? zo : zr;
+    v[i] = box_muller_half(w.x, w.y, strig);
+    v[i + P / 2] = box_muller_half(w.z, w.w, strig);
   }
 }
 
@@ -81,19 +75,18 @@ __global__ void __launch_bounds__(256, 3) noise_pair_fast(ColArgs a) {
   __syncthreads();
 
   const int M = g.M;
-  const uint64_t key = g.seed + (uint64_t)(g.field0 + (int64_t)blockIdx.z);  // uniform
+  const uint64_t key = field_key(g, blockIdx.z);  // uniform
+  const float* stab = field_stab(g, blockIdx.z);
   float2 v[P];
 
-  // One column kd of the pair: noise, s_K, the inverse FFT along axis 1.  The
-  // normals are drawn by every lane (their lane shuffles need the whole warp;
-  // with several pairs per CTA the lanes of a warp sit in different columns),
-  // then replaced on the planes kd in {0, M} and zeroed for invalid slots.
+  // One column kd of the pair: noise, s_K, the inverse FFT along axis 1; the
+  // planes kd in {0, M} take the conjugation rule, invalid slots zeros.
   auto column = [&](int kd, bool valid) {
     const int t = CtaCoordsHW{}.tid();
     const int c = t & (CC - 1), tau = t / CC;
-    normals_half_shfl<P, TPT, CC>(v, tau, kd, M, key, strig);
-    const float* srow = g.stab + (size_t)kd * (N / 2 + 1);
+    const float* srow = stab + (size_t)kd * (N / 2 + 1);
     if (kd != 0 && kd != M) {
+      normals_half<P, TPT>(v, tau, 0, kd, 1, M, key, strig);
 #pragma unroll
       for (int q = 0; q < P; ++q) {
         const float s = __ldg(srow + (q < P / 2 ? tau + TPT * q : N - tau - TPT * q));

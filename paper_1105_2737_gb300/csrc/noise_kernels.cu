@@ -1,7 +1,6 @@
 // Launchers of the noise + axis-1 pass (Algorithm 2's first pass: Philox
 // noise, the Hermitian arrangement and s_K in registers, then the inverse FFT
 // along axis 1), in their own translation unit: each radix is compiled once
-// per way of dealing the Philox words to threads (NoiseVariant), and once
 // with and once without pair mode, so that each kernel holds only the code it
 // runs.
 #include "pass_kernels.cuh"
@@ -10,26 +9,13 @@ namespace grf {
 
 namespace {
 
-template <int P, int PAIR>
-cudaError_t launch_noise_nv(const ColArgs& a, dim3 grid, cudaStream_t s) {
-  switch (noise_variant(a.N, P, a.C)) {
-    case NV_INTHREAD: return launch_col_t<P, COL_NOISE, COL_INV, PAIR, NV_INTHREAD>(a, grid, s);
-    case NV_SHFL:
-      if constexpr (P >= 4) return launch_col_t<P, COL_NOISE, COL_INV, PAIR, NV_SHFL>(a, grid, s);
-      return cudaErrorInvalidValue;  // radix 2 is only ever the whole transform (N = 2)
-    default:
-      if constexpr (P >= 4) return launch_col_t<P, COL_NOISE, COL_INV, PAIR, NV_PLAIN>(a, grid, s);
-      return cudaErrorInvalidValue;
-  }
-}
-
 template <int PAIR>
 cudaError_t launch_noise_p(int P, const ColArgs& a, dim3 grid, cudaStream_t s) {
   switch (P) {
-    case 2: return launch_noise_nv<2, PAIR>(a, grid, s);
-    case 4: return launch_noise_nv<4, PAIR>(a, grid, s);
-    case 8: return launch_noise_nv<8, PAIR>(a, grid, s);
-    case 16: return launch_noise_nv<16, PAIR>(a, grid, s);
+    case 2: return launch_col_t<2, COL_NOISE, COL_INV, PAIR>(a, grid, s);
+    case 4: return launch_col_t<4, COL_NOISE, COL_INV, PAIR>(a, grid, s);
+    case 8: return launch_col_t<8, COL_NOISE, COL_INV, PAIR>(a, grid, s);
+    case 16: return launch_col_t<16, COL_NOISE, COL_INV, PAIR>(a, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }

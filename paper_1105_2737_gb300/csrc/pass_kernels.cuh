@@ -11,21 +11,21 @@ namespace grf {
 // and twiddle address of the exchanges is a constant offset.  These forms are
 // compiled for the 256-thread radix-16 geometries (C N = 4096) and chosen by
 // the launchers; LN = CC = 0 is the general kernel.
-template <int P, int SRC, int MODE, int PAIR, int NV, int LN = 0, int CC = 0>
+template <int P, int SRC, int MODE, int PAIR, int LN = 0, int CC = 0>
 __global__ void __launch_bounds__(kMaxThreads<P>, kMinBlocks<P>) col_kernel(ColArgs a) {
   extern __shared__ float2 sm[];
   if constexpr (PAIR) {
-    col_body_pair<P, SRC, MODE, NV, LN, CC>(a, CtaCoordsHW{}, blockDim.x, sm);
+    col_body_pair<P, SRC, MODE, LN, CC>(a, CtaCoordsHW{}, blockDim.x, sm);
   } else {
     const int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    col_body<P, SRC, MODE, NV, LN, CC>(a, blockIdx.x, blockIdx.y, blockIdx.z, blk, blockDim.x, sm);
+    col_body<P, SRC, MODE, LN, CC>(a, blockIdx.x, blockIdx.y, blockIdx.z, blk, blockDim.x, sm);
   }
 }
 
-template <int P, int SRC, int MODE, int LN = 0, int CC = 0, int TT = 0>
+template <int P, int SRC, int MODE, int LN = 0, int CC = 0, int TT = 0, int BZ = -1>
 __global__ void __launch_bounds__(kMaxThreads<P>, kMinBlocks<P>) row_kernel(RowArgs a) {
   extern __shared__ float2 sm[];
-  row_body<P, SRC, MODE, LN, CC, TT>(a, blockIdx.x, blockDim.x, sm);
+  row_body<P, SRC, MODE, LN, CC, TT, BZ>(a, blockIdx.x, blockDim.x, sm);
 }
 
 // log2 N if (N, C) is one of the compile-time radix-16 geometries (C N = 4096,
@@ -74,18 +74,18 @@ __global__ void __launch_bounds__(512) fourstep_stage2(FourStepArgs a) {
   fourstep2_body<P>(a, blockIdx.x, blockIdx.z, blockDim.x, sm);
 }
 
-template <int P, int SRC, int MODE, int PAIR, int NV, int LN = 0, int CC = 0>
+template <int P, int SRC, int MODE, int PAIR, int LN = 0, int CC = 0>
 static cudaError_t launch_col_t(const ColArgs& a, dim3 grid, cudaStream_t s) {
   const int threads = a.C * a.N / P;
   const size_t smem = PAIR ? col_pair_smem_bytes(a.N, a.C) : col_smem_bytes(a.N, a.C);
-  auto k = col_kernel<P, SRC, MODE, PAIR, NV, LN, CC>;
+  auto k = col_kernel<P, SRC, MODE, PAIR, LN, CC>;
   cudaError_t e = prepare_kernel((const void*)k, threads, smem);
   if (e != cudaSuccess) return e;
   k<<<grid, threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int P, int SRC, int MODE, int LN = 0, int CC = 0, int TT = 0>
+template <int P, int SRC, int MODE, int LN = 0, int CC = 0, int TT = 0, int BZ = -1>
 static cudaError_t launch_row_t(const RowArgs& a, dim3 grid, cudaStream_t s) {
   const int threads = a.C * (a.M / P);
   size_t smem = row_smem_bytes(a.M, a.C);
@@ -93,7 +93,7 @@ static cudaError_t launch_row_t(const RowArgs& a, dim3 grid, cudaStream_t s) {
     const size_t need = (size_t)threads * 3 * sizeof(double);
     if (need > smem) smem = need;
   }
-  auto k = row_kernel<P, SRC, MODE, LN, CC, TT>;
+  auto k = row_kernel<P, SRC, MODE, LN, CC, TT, BZ>;
   cudaError_t e = prepare_kernel((const void*)k, threads, smem);
   if (e != cudaSuccess) return e;
   k<<<grid, threads, smem, s>>>(a);

@@ -16,31 +16,6 @@
 
 namespace grf {
 
-// Interior-column normals (z_re + i z_im)/sqrt 2 of the entries
-// k1 = tau + TPT q of column (k2, k3) of a 3-D half spectrum (call
-// ((k1 >> 1) N2 + k2)(M + 1) + k3, words 2 (k1 & 1), +1; rows 2i and 2i + 1 on
-// lanes t and t ^ CC).  Every lane of the warp must take part.
-template <int P, int TPT, int CC>
-GRF_DEV void normals3_half_shfl(float2 (&v)[P], int tau, int k2, int k3, int N2, int M, uint64_t key,
-                                const float2* strig) {
-  const bool odd = (tau & 1) != 0;
-  const uint64_t stride = (uint64_t)(TPT >> 1) * (uint64_t)N2 * (uint64_t)(M + 1);
-  const int k1 = tau + (odd ? TPT * (P / 2) : 0);
-  uint64_t call = ((uint64_t)(k1 >> 1) * (uint64_t)N2 + (uint64_t)k2) * (uint64_t)(M + 1) + (uint64_t)k3;
-#pragma unroll
-  for (int i = 0; i < P / 2; ++i, call += stride) {
-    const u32x4 w = philox_call(call, 0u, key);
-    const uint32_t oa = odd ? w.z : w.x, ob = odd ? w.w : w.y;
-    const uint32_t pa = odd ? w.x : w.z, pb = odd ? w.y : w.w;
-    const uint32_t ra = __shfl_xor_sync(0xffffffffu, pa, CC);
-    const uint32_t rb = __shfl_xor_sync(0xffffffffu, pb, CC);
-    const float2 zo = box_muller_half(oa, ob, strig);
-    const float2 zr = box_muller_half(ra, rb, strig);
-    v[i] = odd ? zr : zo;
-    v[i + P / 2] = odd ? zo : zr;
-  }
-}
-
 // Shared memory: the transform's exchange buffer (also the [c][j1] staging of
 // the radix-R step: CC (N1 + 1) <= CC spad(N1)) and the 256 coarse angles.
 __host__ __device__ constexpr size_t plane3_noise_smem_bytes(int N1, int CC) {
@@ -58,7 +33,7 @@ __global__ void __launch_bounds__(256, 3) plane3_noise_kernel(ColArgs a, PlaneAr
   __syncthreads();
 
   const int M = g.M, N2 = pl.N2, Q = pl.Q;
-  const uint64_t key = g.seed + (uint64_t)(g.field0 + (int64_t)blockIdx.z);  // uniform
+  const uint64_t key = field_key(g, blockIdx.z);  // uniform
   const int kp = blockIdx.y;
   float2 v[P];
   {
@@ -69,10 +44,9 @@ __global__ void __launch_bounds__(256, 3) plane3_noise_kernel(ColArgs a, PlaneAr
     const int k3 = (int)blockIdx.x * U + u;
     const bool valid = k3 <= M;
     const int kd = valid ? k3 : 0;
-    // every lane draws (the shuffles need the whole warp)
-    normals3_half_shfl<P, TPT, CC>(v, tau, k2, kd, N2, M, key, strig);
-    const float* srow = g.stab + ((size_t)kd * (N2 / 2 + 1) + min(k2, N2 - k2)) * (N / 2 + 1);
+    const float* srow = field_stab(g, blockIdx.z) + ((size_t)kd * (N2 / 2 + 1) + min(k2, N2 - k2)) * (N / 2 + 1);
     if (kd != 0 && kd != M) {
+      normals_half<P, TPT>(v, tau, k2, kd, N2, M, key, strig);
 #pragma unroll
       for (int q = 0; q < P; ++q) {
         const float s = __ldg(srow + (q < P / 2 ? tau + TPT * q : N - tau - TPT * q));

@@ -10,7 +10,7 @@ namespace {
 
 template <int PAIR, int LN>
 cudaError_t noise_spec_t(const ColArgs& a, dim3 grid, cudaStream_t s) {
-  return launch_col_t<16, COL_NOISE, COL_INV, PAIR, NV_SHFL, LN, (4096 >> LN)>(a, grid, s);
+  return launch_col_t<16, COL_NOISE, COL_INV, PAIR, LN, (4096 >> LN)>(a, grid, s);
 }
 
 template <int PAIR>
@@ -30,7 +30,7 @@ bool noise_spec(int ln, const ColArgs& a, dim3 grid, cudaStream_t s, cudaError_t
 bool launch_col_noise_spec(int P, const ColArgs& a, dim3 grid, cudaStream_t s, cudaError_t* err) {
   if (launch_noise_pair_fast(P, a, grid, s, err)) return true;
   const int ln = spec_ln(P, a.N, a.C, 256, 4096);
-  if (!ln || noise_variant(a.N, P, a.C) != NV_SHFL) return false;
+  if (!ln) return false;
   return a.zpair ? noise_spec<1>(ln, a, grid, s, err) : noise_spec<0>(ln, a, grid, s, err);
 }
 

@@ -9,19 +9,21 @@ namespace {
 
 template <int LN>
 cudaError_t load_pair_t(const ColArgs& a, dim3 grid, cudaStream_t s) {
-  return launch_col_t<16, COL_LOAD, COL_INV, 1, NV_ANY, LN, (4096 >> LN)>(a, grid, s);
+  return launch_col_t<16, COL_LOAD, COL_INV, 1, LN, (4096 >> LN)>(a, grid, s);
 }
-// the workspace tile T as a compile-time constant (T in {1, 2, 4, 8, 16})
+// the workspace tile T as a compile-time constant (T in {1, 2, 4, 8, 16}) for
+// a plan's fields; a batch plan's launch (outputs by field) keeps T at run time
 template <int LN>
 cudaError_t row_c2r_t(const RowArgs& a, dim3 grid, cudaStream_t s) {
   constexpr int CC = 4096 >> LN;
+  if (a.zout) return launch_row_t<16, ROW_LOAD_Z, ROW_C2R, LN, CC, 0, 1>(a, grid, s);
   switch (a.T) {
-    case 1: return launch_row_t<16, ROW_LOAD_Z, ROW_C2R, LN, CC, 1>(a, grid, s);
-    case 2: return launch_row_t<16, ROW_LOAD_Z, ROW_C2R, LN, CC, 2>(a, grid, s);
-    case 4: return launch_row_t<16, ROW_LOAD_Z, ROW_C2R, LN, CC, 4>(a, grid, s);
-    case 8: return launch_row_t<16, ROW_LOAD_Z, ROW_C2R, LN, CC, 8>(a, grid, s);
-    case 16: return launch_row_t<16, ROW_LOAD_Z, ROW_C2R, LN, CC, 16>(a, grid, s);
-    default: return launch_row_t<16, ROW_LOAD_Z, ROW_C2R, LN, CC>(a, grid, s);
+    case 1: return launch_row_t<16, ROW_LOAD_Z, ROW_C2R, LN, CC, 1, 0>(a, grid, s);
+    case 2: return launch_row_t<16, ROW_LOAD_Z, ROW_C2R, LN, CC, 2, 0>(a, grid, s);
+    case 4: return launch_row_t<16, ROW_LOAD_Z, ROW_C2R, LN, CC, 4, 0>(a, grid, s);
+    case 8: return launch_row_t<16, ROW_LOAD_Z, ROW_C2R, LN, CC, 8, 0>(a, grid, s);
+    case 16: return launch_row_t<16, ROW_LOAD_Z, ROW_C2R, LN, CC, 16, 0>(a, grid, s);
+    default: return launch_row_t<16, ROW_LOAD_Z, ROW_C2R, LN, CC, 0, 0>(a, grid, s);
   }
 }
 

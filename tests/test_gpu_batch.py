@@ -1,6 +1,7 @@
-"""Uneven batches in one persistent launch: every field against the oracle,
-graph replay against the plain launch, shard invariance, and the bounded wait
-that turns a dependency that never resolves into GRF_ERR_TIMEOUT."""
+"""Uneven batches, in both modes (per-shape launches in one graph; one
+persistent kernel): every field against the oracle, graph replay against the
+plain launch, the two modes against each other, shard invariance, and the
+bounded wait that turns a dependency that never resolves into GRF_ERR_TIMEOUT."""
 import numpy as np
 import pytest
 
@@ -32,10 +33,11 @@ def _oracle_field(shape, L, spec, key):
     return O.alg2_field(shape, L, O.Spectrum(O.MATERN, spec["sigma"], spec["ell"], spec["nu"]), key)
 
 
-def test_every_field_matches_the_oracle():
+@pytest.mark.parametrize("mode", ["shapes", "persistent"])
+def test_every_field_matches_the_oracle(mode):
     shapes, lengths, specs = _small_batch()
     assert len({len(s) for s in shapes}) == 3  # 1-D, 2-D and 3-D all present
-    b = _api().GRFBatch(shapes, lengths, specs)
+    b = _api().GRFBatch(shapes, lengths, specs, mode=mode)
     outs = b.sample(seed=500)
     torch.cuda.synchronize()
     assert b.status() == 0
@@ -46,11 +48,12 @@ def test_every_field_matches_the_oracle():
         assert rel <= 2e-6 and np.abs(got - ref).max() <= 1e-5, (i, shp, rel)
 
 
-def test_graph_replay_equals_plain_launch():
+@pytest.mark.parametrize("mode", ["shapes", "persistent"])
+def test_graph_replay_equals_plain_launch(mode):
     shapes, lengths, specs = _small_batch(24, seed=4)
-    b = _api().GRFBatch(shapes, lengths, specs)
+    b = _api().GRFBatch(shapes, lengths, specs, mode=mode)
     outs = b.empty()
-    for seed in (10, 99):
+    for seed in (10, 99, 10):
         b.sample(seed=seed, outs=outs)
         ref = [o.clone() for o in outs]
         for o in outs:
@@ -61,6 +64,25 @@ def test_graph_replay_equals_plain_launch():
         for o, r in zip(outs, ref):
             assert torch.equal(o, r)
     assert b.status() == 0
+
+
+def test_modes_draw_the_same_fields():
+    """Per-shape launches and the persistent kernel: the same fields up to FP32 rounding."""
+    shapes, lengths, specs = _small_batch(30, seed=8)
+    a = _api().GRFBatch(shapes, lengths, specs, mode="shapes").sample(seed=77)
+    p = _api().GRFBatch(shapes, lengths, specs, mode="persistent").sample(seed=77)
+    torch.cuda.synchronize()
+    for x, y in zip(a, p):
+        x, y = x.double(), y.double()
+        assert float((x - y).norm() / y.norm()) <= 2e-6 and float((x - y).abs().max()) <= 1e-5
+
+
+def test_invalid_mode_is_rejected():
+    from paper_1105_2737_gb300 import _lib as L
+    shapes, lengths, specs = _small_batch(4, seed=9)
+    b = _api().GRFBatch(shapes, lengths, specs)
+    with pytest.raises(L.GRFError):
+        L.grf_batch_set_mode(b.handle, 2)
 
 
 def test_shard_invariance():
@@ -110,4 +132,4 @@ def test_full_size_uneven_batch():
         ref = _oracle_field(shapes[i], lengths[i], specs[i], i)
         got = outs[i].cpu().numpy().astype(np.float64)
         rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-        assert rel <= 2e-6, (i, shapes[i], rel)
+        assert rel <= 2e-6 and np.abs(got - ref).max() <= 1e-5, (i, shapes[i], rel)

@@ -3,9 +3,9 @@ it times them, compared with the FP64 oracle element by element.
 
 * 2-D 4096^2 x 64 in the schedule the tuner picks on this GPU (the bench tunes
   before it times): fields 0 and 63 whole, every one of their 16.7 M points.
-* The 4096-field uneven batch in one persistent launch: the largest 2-D, 3-D
-  and 1-D fields of the batch (1024-side 2-D, 128^3, 2^20) and a spread of
-  small ones, whole, with relative L2 and max abs.
+* The 4096-field uneven batch, per-shape launches and one persistent launch:
+  the largest 2-D, 3-D and 1-D fields of the batch (1024-side 2-D, 128^3,
+  2^20) and a spread of small ones, whole, with relative L2 and max abs.
 * 3-D 512^3 x 1 (Gaussian, ell = 0.03): sampled lines of the field (the
   oracle's half spectrum is 67 M modes; each line is a dense contraction).
 
@@ -58,12 +58,13 @@ def test_headline_whole_fields_tuned_schedule():
     g.close()
 
 
-def test_full_size_uneven_batch_every_kind():
+@pytest.mark.parametrize("mode", ["shapes", "persistent"])
+def test_full_size_uneven_batch_every_kind(mode):
     """The 4096-field uneven batch: the largest 2-D field, the largest 3-D field,
     the longest 1-D field and the first eight small fields, whole, against the oracle."""
     from paper_1105_2737_gb300.inputs import uneven_batch
     shapes, lengths, specs = uneven_batch(4096, seed=0)
-    b = _api().GRFBatch(shapes, lengths, specs)
+    b = _api().GRFBatch(shapes, lengths, specs, mode=mode)
     outs = b.sample(seed=0)
     torch.cuda.synchronize()
     assert b.status() == 0
