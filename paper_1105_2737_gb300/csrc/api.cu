@@ -552,8 +552,15 @@ grf_status sample_chunk_fp32(grf_plan p, uint64_t seed, int64_t f0, int64_t nb, 
     pl.tw = p->tw;
     pl.tws = p->tw + 2 * p->twmax;
     pl.status = p->status;
-    const ColArgs a = col_axis1(p, g, nullptr, ws, 1);
-    TLAUNCH(GRF_KERNEL_NOISE_COLUMNS, launch_plane3_noise(a, pl, nb, s), "3-D plane pass 1");
+    ColArgs a = col_axis1(p, g, nullptr, ws, 1);
+    if (p->N1 >= 256) {
+      TLAUNCH(GRF_KERNEL_NOISE_COLUMNS, launch_plane3_noise(a, pl, nb, s), "3-D plane pass 1");
+    } else {  // the column pass, whole planes with padded rows
+      a.pitch3 = pl.S3;
+      a.bstride = (int64_t)p->N1 * p->Nmid * pl.S3;
+      TLAUNCH(GRF_KERNEL_NOISE_COLUMNS, launch_col(COL_NOISE, COL_INV, p->colA.P, a, col_grid(a, 1, nb), s),
+              "3-D plane pass 1");
+    }
     if (st && st != s) {
       GRF_CUDA(cudaEventRecord(ev, s), "pipeline event");
       GRF_CUDA(cudaStreamWaitEvent(st, ev, 0), "pipeline wait");

@@ -225,6 +225,7 @@ struct BatchPlan {
   int64_t* zfield = nullptr;         // device copy of class_order
   float** zouts = nullptr;           // output pointers, class-ordered
   uint64_t* seed_dev = nullptr;
+  int* status_dev = nullptr;  // the plan's status word (the plane path's bulk-copy waits report here)
   static constexpr int kStreams = 8;
   cudaStream_t cstreams[kStreams] = {};
   cudaEvent_t cfork = nullptr, cjoin[kStreams] = {};
@@ -549,6 +550,41 @@ cudaError_t launch_class(BatchPlan* b, const BatchPlan::ShapeClass& c, cudaStrea
     fs.C = C2;
     return launch_fourstep(2, 16, fs, nf, s);
   }
+  if (d == 3 && plane3_radix(N1, Nmid, M)) {  // two passes: whole (sub-)planes in shared memory
+    PlaneArgs pl{};
+    pl.N1 = N1;
+    pl.N2 = Nmid;
+    pl.M = M;
+    pl.R = plane3_radix(N1, Nmid, M);
+    pl.Q = Nmid / pl.R;
+    pl.S3 = M + 2;
+    pl.ws = ws;
+    pl.tw = b->tw;
+    pl.tws = tws;
+    pl.status = b->status_dev;
+    pl.zout = zout;
+    ColArgs a{};
+    a.N = N1;
+    a.logN = lg2(N1);
+    a.ncols = (int64_t)Nmid * (M + 1);
+    a.T = 1;
+    a.logT = 0;
+    a.bstride = (int64_t)N1 * Nmid * pl.S3;
+    a.out = ws;
+    a.tw = b->tw + N1;
+    a.tws = tws;
+    a.plane_is_k1 = 1;
+    a.g = g;
+    if (N1 >= 256) {
+      e = launch_plane3_noise(a, pl, nf, s);
+    } else {
+      a.pitch3 = pl.S3;
+      a.C = tile_cols(N1, a.ncols, 256);
+      e = launch_col(COL_NOISE, COL_INV, 16, a, dim3((unsigned)((a.ncols + a.C - 1) / a.C), 1, (unsigned)nf), s);
+    }
+    if (e != cudaSuccess) return e;
+    return launch_plane3_c2r(pl, nf, s);
+  }
   const int T = (d == 2 && N1 >= 256) ? 8 : 1;
   const int64_t hsize = (int64_t)N1 * Nmid * (M + 1);
   ColArgs a{};
@@ -762,6 +798,7 @@ grf_status batch_plan_build(BatchPlan** out, int64_t count, const int* d, const 
       const int N1 = f0.d >= 2 ? f0.n[0] : 1, Nmid = f0.d == 3 ? f0.n[1] : 1;
       c.fold = (int64_t)(N1 / 2 + 1) * (Nmid / 2 + 1) * (M + 1);
       c.wstride = f0.d == 1 ? M : (int64_t)N1 * Nmid * (M + 1);
+      if (f0.d == 3 && plane3_radix(N1, Nmid, M)) c.wstride = (int64_t)plane3_ws_entries(N1, Nmid, M);
       c.stab_off = stab_total;
       c.ws_off = ws_total;
       c.points = f0.points * c.nf;
@@ -810,6 +847,7 @@ grf_status batch_plan_build(BatchPlan** out, int64_t count, const int* d, const 
   if (e == cudaSuccess) e = cudaMalloc(&b->zouts, (size_t)count * sizeof(float*));
   if (e == cudaSuccess) e = cudaMalloc(&b->zfield, (size_t)count * sizeof(int64_t));
   if (e == cudaSuccess) e = cudaMalloc(&b->seed_dev, sizeof(uint64_t));
+
   if (e == cudaSuccess)
     e = cudaMemcpy(b->zfield, b->class_order.data(), (size_t)count * sizeof(int64_t), cudaMemcpyHostToDevice);
   for (int q = 0; q < BatchPlan::kStreams && e == cudaSuccess; ++q) {
@@ -922,6 +960,7 @@ grf_status batch_plan_sample(BatchPlan* b, uint64_t seed, void* const* out, cuda
     *err = std::string("batch sample: ") + cudaGetErrorString(e);
     return GRF_ERR_CUDA;
   }
+  b->status_dev = status;
   if (b->mode == 0 && b->withhold < 0) return sample_classes(b, seed, s, use_graph, err);
   if (e == cudaSuccess && !b->tuned) {
     const char* env = std::getenv("GRF_TUNE");

@@ -342,8 +342,14 @@ GRF_DEV void col_body(const ColArgs& a, int bx, int by, int64_t bz, int64_t blk,
   }
 
   if (valid) {
+    if (a.pitch3) {  // padded rows for the plane path's sub-plane kernel
+      const int64_t scol = (int64_t)cg.kmid * a.pitch3 + cg.kd, rstride = (int64_t)a.g.Nmid * a.pitch3;
 #pragma unroll
-    for (int q = 0; q < P; ++q) a.out[base + col_offset(a, tau + TPT * q, col)] = v[q];
+      for (int q = 0; q < P; ++q) a.out[base + (int64_t)(tau + TPT * q) * rstride + scol] = v[q];
+    } else {
+#pragma unroll
+      for (int q = 0; q < P; ++q) a.out[base + col_offset(a, tau + TPT * q, col)] = v[q];
+    }
   }
 }
 

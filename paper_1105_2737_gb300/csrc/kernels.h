@@ -61,6 +61,8 @@ struct ColArgs {
   const float2* tw;   // tw[k] = exp(2 pi i k / N)
   const float2* tws;  // radix-16 stage tables (see fft_core)
   int plane_is_k1;   // COL_NOISE / scale / adjoint: the transform axis is axis 1
+  int pitch3;        // 3-D noise pass of the plane path (T = 1): store (j1, k2, k3) at
+                     // (j1 N2 + k2) pitch3 + k3 (rows padded to pitch3 = M + 2; 0: off)
   int zpair;         // COL_INV / COL_FWD_SCALE_INV on a plane of M+1 columns: slot p takes
                      // columns p and M - p and writes Z of the c2r split (see col_body)
   const float2* twz; // zpair: exp(2 pi i k / N_d), k <= M/2
@@ -163,8 +165,11 @@ struct PlaneArgs {
   const float2* tw;    // tw[L + k] = exp(2 pi i k / L)
   const float2* tws;   // stage tables (see fft_core)
   int* status;         // GRF_ERR_TIMEOUT if a bulk copy's wait ran out
+  float* const* zout;  // batch plans: output of the field at launch index z (NULL: out)
 };
-// R for a 3-D plan (1, 2 or 4), or 0 if the plane path does not apply.
+// R for a 3-D plan (1, 2 or 4), or 0 if the plane path does not apply.  For
+// N1 < 256 pass 1 is the ordinary noise + axis-1 column pass writing whole
+// planes (R = 1) with rows padded to M + 2 (ColArgs::pitch3).
 int plane3_radix(int N1, int N2, int M);
 size_t plane3_ws_entries(int N1, int N2, int M);  // per field
 cudaError_t launch_plane3_noise(const ColArgs& a, const PlaneArgs& pl, int64_t nfields, cudaStream_t s);

@@ -87,7 +87,8 @@ GRF_DEV void plane3_subplane(const PlaneArgs& pl, float2* sub, float2* xb, int64
   const int R = pl.R;
   const int64_t fj = id / R;  // field N1 + j1
   const int s = (int)(id - fj * R);
-  float* plane = pl.out + fj * (int64_t)pl.N2 * (2 * M);
+  float* plane = pl.zout ? pl.zout[fj / pl.N1] + (fj % pl.N1) * (int64_t)pl.N2 * (2 * M)
+                         : pl.out + fj * (int64_t)pl.N2 * (2 * M);
   const float2* twM = pl.tw + M;
   const float2* twN = pl.tw + 2 * M;
   for (int r0 = 0; r0 < Q; r0 += RB) {
@@ -195,7 +196,12 @@ bool pow2i(int x) { return x > 0 && (x & (x - 1)) == 0; }
 }  // namespace
 
 int plane3_radix(int N1, int N2, int M) {
-  if (!pow2i(N1) || !pow2i(N2) || !pow2i(M) || N1 < 256 || N1 > 1024) return 0;
+  if (!pow2i(N1) || !pow2i(N2) || !pow2i(M) || N1 < 2 || N1 > 1024) return 0;
+  if (N1 < 256) {  // the column pass writes whole planes (R = 1) with padded rows
+    const int LQ = lg(N2), LM = lg(M);
+    if (!(LQ >= 4 && LQ <= 7 && LM >= 4 && LM <= 9)) return 0;
+    return plane3_c2r_smem_bytes(N2, M) <= 227 * 1024 ? 1 : 0;
+  }
   const int CC = 4096 / N1;
   int fallback = 0;
   // pass 1 writes runs of U = CC / R consecutive k3: at least 4 (32 bytes), or
@@ -258,7 +264,7 @@ cudaError_t launch_plane3_noise(const ColArgs& a, const PlaneArgs& pl, int64_t n
 
 cudaError_t launch_plane3_c2r(const PlaneArgs& pl, int64_t nfields, cudaStream_t s) {
   if (pl.R < 1 || pl.Q * pl.R != pl.N2 || pl.S3 != pl.M + 2 || nfields < 1 || !pl.status) return cudaErrorInvalidValue;
-  if ((reinterpret_cast<uintptr_t>(pl.ws) & 15) || (reinterpret_cast<uintptr_t>(pl.out) & 15))
+  if ((reinterpret_cast<uintptr_t>(pl.ws) & 15) || (!pl.zout && (reinterpret_cast<uintptr_t>(pl.out) & 15)))
     return cudaErrorInvalidValue;
   if (nfields * pl.N1 * pl.R >= (int64_t(1) << 31)) return cudaErrorInvalidValue;
   switch (lg(pl.Q)) {

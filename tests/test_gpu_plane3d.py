@@ -1,7 +1,8 @@
 """The 3-D plane path (pass 1: noise, axis 1 and the first radix-R step of
 axis 2; pass 2: one sub-plane per CTA, staged by a bulk copy, the rest of axis
 2 and the c2r rows, rows written by bulk copies) against the FP64 oracle, for
-every split R of axis 2 it takes (1, 2, 4), transform lengths N1 = 256..1024,
+every split R of axis 2 it takes (1, 2, 4), transform lengths N1 = 8..1024 (below
+256 pass 1 is the ordinary column pass writing whole planes with padded rows),
 both forms of pass 2 (two slots per persistent CTA, one slot per CTA), ragged
 k3 groups (M + 1 is odd), several fields per launch and plans the path does not
 take; and against the three-pass form (GRF_PLANE3=0) on the same seeds."""
@@ -51,6 +52,9 @@ CASES = [((256, 16, 256), 1, 2, O.Spectrum(O.MATERN, 1.0, 0.05, 1.5)),
          ((256, 256, 512), 4, 1, O.Spectrum(O.MATERN, 1.0, 0.05, 2.5)),   # one slot, 512 threads
          ((512, 256, 64), 2, 2, O.Spectrum(O.MATERN, 1.3, 0.05, 1.5)),
          ((1024, 64, 128), 1, 2, O.Spectrum(O.MATERN, 1.0, 0.1, 1.5)),
+         ((128, 128, 128), 1, 2, O.Spectrum(O.GAUSSIAN, 1.0, 0.03)),      # pass 1: the column pass, padded rows
+         ((8, 32, 64), 1, 3, O.Spectrum(O.MATERN, 1.0, 0.1, 1.5)),
+         ((64, 16, 128), 1, 2, O.Spectrum(O.MATERN, 1.0, 0.05, 2.5)),
          ((512, 512, 512), 0, 1, O.Spectrum(O.GAUSSIAN, 1.0, 0.03)),      # runs of 4 k3 need R <= 2
          ((2048, 16, 32), 0, 3, O.Spectrum(O.MATERN, 1.0, 0.05, 1.5))]
 
