@@ -163,6 +163,13 @@ def _oracle_all_cores(shape=SHAPE):
 
 def _cpu_model() -> str:
     try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for ln in r.stdout.splitlines():
+            if ln.strip().startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
         with open("/proc/cpuinfo") as f:
             txt = f.read()
         for key in ("model name", "Model", "CPU part"):
