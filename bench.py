@@ -402,7 +402,7 @@ def run_ours(args):
     g3.close()
     del o3
 
-    # uneven batch: 4096 fields (60 % 2-D, 30 % 1-D, 10 % 3-D) in one persistent launch
+    # uneven batch: 4096 fields (60 % 2-D, 30 % 1-D, 10 % 3-D), per-shape launches and one persistent launch
     from paper_1105_2737_gb300.api import GRFBatch
     from paper_1105_2737_gb300.inputs import uneven_batch
     ushapes, ulengths, uspecs = uneven_batch(4096, seed=0)

@@ -510,8 +510,8 @@ grf_status sample_chunk_fp32(grf_plan p, uint64_t seed, int64_t f0, int64_t nb, 
     f.logB = ilog2(p->fsB);
     f.M = p->M;
     f.N = 2 * p->M;
-    f.T = p->fsC1;
-    f.logT = ilog2(p->fsC1);
+    f.T = p->fsC1 / 2;  // stage 1 takes fsC1 / 2 mirror pairs of columns per CTA
+    f.logT = ilog2(p->fsC1 / 2);
     f.Y = p->ws;
     f.Yin = p->ws;
     f.out = out;
@@ -525,7 +525,7 @@ grf_status sample_chunk_fp32(grf_plan p, uint64_t seed, int64_t f0, int64_t nb, 
     f.seed = seed;
     f.field0 = f0;
     f.C = p->fsC1;
-    TLAUNCH(GRF_KERNEL_ROWS_1D, launch_fourstep(1, 16, f, nb, s), "four-step stage 1");
+    TLAUNCH(GRF_KERNEL_ROWS_1D, launch_fourstep(3, 16, f, nb, s), "four-step stage 1");
     f.C = p->fsC2;
     TLAUNCH(GRF_KERNEL_ROWS_1D, launch_fourstep(2, 16, f, nb, s), "four-step stage 2");
     return GRF_OK;

@@ -530,8 +530,8 @@ cudaError_t launch_class(BatchPlan* b, const BatchPlan::ShapeClass& c, cudaStrea
     fs.M = M;
     fs.N = Nd;
     const int C1 = std::min(4096 / fs.B, fs.A), C2 = std::min(4096 / fs.A, fs.B);
-    fs.T = C1;
-    fs.logT = lg2(C1);
+    fs.T = C1 / 2;  // stage 1 in mirror pairs: C1 / 2 pairs per CTA
+    fs.logT = lg2(C1 / 2);
     fs.Y = ws;
     fs.Yin = ws;
     fs.twA = b->tw + fs.A;
@@ -546,7 +546,7 @@ cudaError_t launch_class(BatchPlan* b, const BatchPlan::ShapeClass& c, cudaStrea
     fs.seed_ptr = g.seed_ptr;
     fs.zout = zout;
     fs.C = C1;
-    if ((e = launch_fourstep(1, 16, fs, nf, s)) != cudaSuccess) return e;
+    if ((e = launch_fourstep(3, 16, fs, nf, s)) != cudaSuccess) return e;
     fs.C = C2;
     return launch_fourstep(2, 16, fs, nf, s);
   }

@@ -601,6 +601,71 @@ GRF_DEV void fourstep1_body(const FourStepArgs& a, int bx, int64_t bz, int nthr,
   }
 }
 
+// Stage 1 with mirror-closed columns: Z[k] needs X[k] and X[M - k], and the
+// entries of column k1 mirror those of column A - k1 (M - k1 - A k2 =
+// (A - k1) + A (B - 1 - k2); column 0 mirrors itself, M - A k2 = A (B - k2),
+// with X[M] for k2 = 0; column A/2 mirrors itself too).  A CTA takes H = C/2
+// pairs p in [bx H, bx H + H): slot c < H holds column p = bx H + c, slot
+// c >= H column A - p' with p' = bx H + (C - 1 - c) (ascending in c), so slot
+// c and slot C - 1 - c are mirrors.  Each X is drawn once, staged in shared
+// memory, and read back by the thread that forms its mirror's Z.  Y is written
+// with tile T = H (a.T), the second half's run straddling two tiles.
+template <int P>
+GRF_DEV void fourstep1_pair_body(const FourStepArgs& a, int bx, int64_t bz, int nthr, float2* sm) {
+  const int C = a.C, H = C / 2;
+  const int t = threadIdx.x;
+  const int c = t & (C - 1);
+  const int tau = t / C;
+  const int TPT = a.B / P;
+  const int half = a.A / 2;
+  int k1;
+  bool valid;
+  if (c < H) {
+    k1 = bx * H + c;
+    valid = k1 <= half;
+  } else {
+    const int p = bx * H + (C - 1 - c);
+    k1 = a.A - p;
+    valid = p >= 1 && p < half;
+  }
+  if (!valid) k1 = 0;
+  const int64_t field = bz;
+  const uint64_t key = (a.seed_ptr ? *a.seed_ptr : a.seed) + (uint64_t)(a.zfield ? a.zfield[field] : a.field0 + field);
+  const float* stab = a.stab + field * a.stab_zstride;
+  // X of this slot's entries k = k1 + A k2, k2 = tau + TPT q, staged as [c][k2] (pitch B + 1)
+  const int pitch = a.B + 1;
+  float2 v[P];
+#pragma unroll
+  for (int q = 0; q < P; ++q) {
+    const int k = k1 + a.A * (tau + TPT * q);
+    v[q] = valid ? x1d(k, a.M, stab, key, a.trig) : make_float2(0.f, 0.f);
+  }
+  cta_sync(nthr);  // the exchange buffer may still be read by a previous use
+#pragma unroll
+  for (int q = 0; q < P; ++q) sm[c * pitch + tau + TPT * q] = v[q];
+  cta_sync(nthr);
+  // Z[k] from X[k] and its mirror
+  const bool self = k1 == 0 || k1 == half;
+  const int mc = self ? c : C - 1 - c;
+#pragma unroll
+  for (int q = 0; q < P; ++q) {
+    const int k2 = tau + TPT * q;
+    const int k = k1 + a.A * k2;
+    float2 xm;
+    if (k1 == 0) xm = k2 == 0 ? x1d(a.M, a.M, stab, key, a.trig) : sm[mc * pitch + a.B - k2];
+    else xm = sm[mc * pitch + a.B - 1 - k2];
+    v[q] = c2r_pre(v[q], xm, __ldg(a.twN + k));
+  }
+  fft_core<P, +1>(v, sm, tau, c, C, a.B, a.logB, a.twB, a.tws, nthr);
+  if (!valid) return;
+  float2* Y = a.Y + field * (int64_t)a.M + ((k1 >> a.logT) * (int64_t)a.B << a.logT) + (k1 & (a.T - 1));
+#pragma unroll
+  for (int q = 0; q < P; ++q) {
+    const int n2 = tau + TPT * q;
+    Y[(int64_t)n2 << a.logT] = cmul(v[q], __ldg(a.twM + n2 * k1));
+  }
+}
+
 template <int P>
 GRF_DEV void fourstep2_body(const FourStepArgs& a, int bx, int64_t bz, int nthr, float2* sm) {
   const int C = a.C;

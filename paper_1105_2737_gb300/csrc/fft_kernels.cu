@@ -128,12 +128,19 @@ static cudaError_t launch_row_p(int P, const RowArgs& a, dim3 grid, cudaStream_t
 
 template <int P>
 static cudaError_t launch_fourstep_t(int stage, const FourStepArgs& a, int64_t nfields, cudaStream_t s) {
-  const int len = stage == 1 ? a.B : a.A;
-  const int ncols = stage == 1 ? a.A : a.B;
+  const int len = stage == 2 ? a.A : a.B;  // stages 1 and 3 transform along k2 (length B)
+  const int ncols = stage == 2 ? a.B : a.A;
   const int threads = a.C * len / P;
   const size_t smem = col_smem_bytes(len, a.C);
   const dim3 grid((unsigned)(ncols / a.C), 1, (unsigned)nfields);
-  if (stage == 1) {
+  if (stage == 3) {  // stage 1 with mirror-closed columns: C / 2 column pairs per CTA
+    const int H = a.C / 2;
+    if (H < 1) return cudaErrorInvalidValue;
+    auto k = fourstep_stage1_pair<P>;
+    cudaError_t e = prepare_kernel((const void*)k, threads, smem);
+    if (e != cudaSuccess) return e;
+    k<<<dim3((unsigned)((a.A / 2 + 1 + H - 1) / H), 1, (unsigned)nfields), threads, smem, s>>>(a);
+  } else if (stage == 1) {
     auto k = fourstep_stage1<P>;
     cudaError_t e = prepare_kernel((const void*)k, threads, smem);
     if (e != cudaSuccess) return e;

@@ -117,6 +117,8 @@ struct FourStepArgs {
   const uint64_t* seed_ptr;
   float* const* zout;
 };
+// stage 1, 2, or 3 = stage 1 with mirror-closed column pairs (a.C / 2 pairs per
+// CTA, Y tile a.T = a.C / 2; each X drawn once, see fourstep1_pair_body).
 cudaError_t launch_fourstep(int stage, int P, const FourStepArgs& a, int64_t nfields, cudaStream_t s);
 
 // One axis of a Neumann / Dirichlet field (r2r.cu): lines of N + 1 points

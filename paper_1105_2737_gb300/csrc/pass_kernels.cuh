@@ -69,6 +69,12 @@ __global__ void __launch_bounds__(512) fourstep_stage1(FourStepArgs a) {
 }
 
 template <int P>
+__global__ void __launch_bounds__(512) fourstep_stage1_pair(FourStepArgs a) {
+  extern __shared__ float2 sm[];
+  fourstep1_pair_body<P>(a, blockIdx.x, blockIdx.z, blockDim.x, sm);
+}
+
+template <int P>
 __global__ void __launch_bounds__(512) fourstep_stage2(FourStepArgs a) {
   extern __shared__ float2 sm[];
   fourstep2_body<P>(a, blockIdx.x, blockIdx.z, blockDim.x, sm);
