@@ -149,6 +149,7 @@ struct grf_plan_s {
   float2* tw = nullptr;
   int twmax = 0;
   float* stab = nullptr;
+  float* stabT = nullptr;  // 1-D four-step: s_k laid out along k2 (build_stab_fourstep)
   float* dstab = nullptr;
   float2* ws = nullptr;
   int64_t chunk = 1;
@@ -221,6 +222,7 @@ void free_plan(grf_plan p) {
   if (!p) return;
   cudaFree(p->tw);
   cudaFree(p->stab);
+  cudaFree(p->stabT);
   cudaFree(p->bctab);
   cudaFree(p->dstab);
   cudaFree(p->ws);
@@ -521,6 +523,9 @@ grf_status sample_chunk_fp32(grf_plan p, uint64_t seed, int64_t f0, int64_t nb, 
     f.twN = twp(p, 2 * p->M);
     f.tws = p->tw + 2 * p->twmax;
     f.stab = p->stab;
+    f.stabT = p->stabT;
+    f.tw2B = twp(p, 2 * p->fsB);
+    f.twMA = twp(p, p->fsA);
     f.trig = p->tw + 256;
     f.seed = seed;
     f.field0 = f0;
@@ -850,6 +855,8 @@ grf_status grf_plan_create(grf_plan* out, int d, const int64_t* n, const double*
       if (p->fsC2 > p->fsB) p->fsC2 = p->fsB;
       p->chunk = max_batch;
       PLAN_CUDA(dmalloc(&p->ws, (size_t)(p->chunk * p->M)), "four-step workspace");
+      PLAN_CUDA(dmalloc(&p->stabT, (size_t)p->M), "four-step s table");
+      PLAN_CUDA(build_stab_fourstep(p->stabT, p->stab, p->fsA, p->fsB, s), "four-step s table build");
     } else if (d == 1) {
       p->row = choose_row(p->M, max_batch);
     } else {
@@ -920,6 +927,7 @@ grf_status grf_plan_set_spectrum(grf_plan p, const grf_spectrum* spec, void* str
     double dig = 0.0;
     if (spec->family == 0) dig = digamma_host(spec->nu + 0.5 * p->d) - digamma_host(spec->nu);
     LAUNCH(build_stab(p->stab, p->dstab, sp, dig, s), "s table build");
+    if (p->stabT) LAUNCH(build_stab_fourstep(p->stabT, p->stab, p->fsA, p->fsB, s), "four-step s table build");
   } else {
     LAUNCH(build_stab_d(p->stab64, sp, s), "FP64 s table build");
   }

@@ -218,7 +218,9 @@ struct BatchPlan {
     int64_t ws_off = 0, wstride = 0;
     int64_t points = 0;
     int stream = 0;
+    int64_t stabT_off = -1;  // 1-D four-step: s_k along k2, M per field
   };
+  float* stabsT = nullptr;
   int mode = 0;  // 0: per-shape launches, 1: one persistent kernel
   std::vector<ShapeClass> classes;
   std::vector<int64_t> class_order;  // batch index of each class-ordered slot
@@ -541,6 +543,10 @@ cudaError_t launch_class(BatchPlan* b, const BatchPlan::ShapeClass& c, cudaStrea
     fs.tws = tws;
     fs.stab = g.stab;
     fs.stab_zstride = c.fold;
+    fs.stabT = b->stabsT + c.stabT_off;
+    fs.stabT_zstride = M;
+    fs.tw2B = b->tw + 2 * fs.B;
+    fs.twMA = b->tw + fs.A;
     fs.trig = g.trig;
     fs.zfield = g.zfield;
     fs.seed_ptr = g.seed_ptr;
@@ -875,6 +881,22 @@ grf_status batch_plan_build(BatchPlan** out, int64_t count, const int* d, const 
     }
     e = build_stab(b->stabs + f.stab_off, nullptr, sp, 0.0, 0);
   }
+  {  // s_k along k2 for the 1-D classes that take the four-step
+    int64_t tot = 0;
+    for (auto& c : b->classes)
+      if (c.d == 1 && c.n[0] / 2 > 4096) {
+        c.stabT_off = tot;
+        tot += c.nf * (int64_t)(c.n[0] / 2);
+      }
+    if (e == cudaSuccess && tot) e = cudaMalloc(&b->stabsT, (size_t)tot * sizeof(float));
+    for (const auto& c : b->classes) {
+      if (e != cudaSuccess || c.stabT_off < 0) continue;
+      const int M = c.n[0] / 2, lm = lg2(M);
+      const int B = 1 << ((lm + 1) / 2), A = M / B;
+      for (int64_t r = 0; r < c.nf && e == cudaSuccess; ++r)
+        e = build_stab_fourstep(b->stabsT + c.stabT_off + r * M, b->stabs + c.stab_off + r * c.fold, A, B, 0);
+    }
+  }
   if (e == cudaSuccess) {
     std::vector<int> v;
     if (tune_cache_lookup(b->signature, &v) && v.size() == 2 && (v[0] == 128 || v[0] == 256) && v[1] >= 1 &&
@@ -1065,6 +1087,7 @@ void batch_plan_free(BatchPlan* b) {
   cudaFree(b->seed_dev);
   cudaFree(b->tw);
   cudaFree(b->stabs);
+  cudaFree(b->stabsT);
   cudaFree(b->ws);
   cudaFree(b->jobs);
   cudaFree(b->items);

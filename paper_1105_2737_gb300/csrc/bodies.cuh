@@ -632,37 +632,42 @@ GRF_DEV void fourstep1_pair_body(const FourStepArgs& a, int bx, int64_t bz, int 
   const int64_t field = bz;
   const uint64_t key = (a.seed_ptr ? *a.seed_ptr : a.seed) + (uint64_t)(a.zfield ? a.zfield[field] : a.field0 + field);
   const float* stab = a.stab + field * a.stab_zstride;
+  const float* srow = a.stabT + field * a.stabT_zstride + (int64_t)k1 * a.B;  // s_{k1 + A k2} at k2
   // X of this slot's entries k = k1 + A k2, k2 = tau + TPT q, staged as [c][k2] (pitch B + 1)
   const int pitch = a.B + 1;
   float2 v[P];
 #pragma unroll
   for (int q = 0; q < P; ++q) {
-    const int k = k1 + a.A * (tau + TPT * q);
-    v[q] = valid ? x1d(k, a.M, stab, key, a.trig) : make_float2(0.f, 0.f);
+    const int k2 = tau + TPT * q;
+    const int k = k1 + a.A * k2;
+    v[q] = valid ? cscale(alg2_xi_1d(k, a.M, key, a.trig), __ldg(srow + k2)) : make_float2(0.f, 0.f);
   }
   cta_sync(nthr);  // the exchange buffer may still be read by a previous use
 #pragma unroll
   for (int q = 0; q < P; ++q) sm[c * pitch + tau + TPT * q] = v[q];
   cta_sync(nthr);
-  // Z[k] from X[k] and its mirror
+  // Z[k] from X[k] and its mirror; e^{2 pi i k / N} = e^{2 pi i k1 / N} e^{2 pi i k2 / (2B)}
   const bool self = k1 == 0 || k1 == half;
   const int mc = self ? c : C - 1 - c;
+  const float2 wk1 = __ldg(a.twN + k1);
 #pragma unroll
   for (int q = 0; q < P; ++q) {
     const int k2 = tau + TPT * q;
-    const int k = k1 + a.A * k2;
     float2 xm;
     if (k1 == 0) xm = k2 == 0 ? x1d(a.M, a.M, stab, key, a.trig) : sm[mc * pitch + a.B - k2];
     else xm = sm[mc * pitch + a.B - 1 - k2];
-    v[q] = c2r_pre(v[q], xm, __ldg(a.twN + k));
+    v[q] = c2r_pre(v[q], xm, cmul(wk1, __ldg(a.tw2B + k2)));
   }
   fft_core<P, +1>(v, sm, tau, c, C, a.B, a.logB, a.twB, a.tws, nthr);
   if (!valid) return;
   float2* Y = a.Y + field * (int64_t)a.M + ((k1 >> a.logT) * (int64_t)a.B << a.logT) + (k1 & (a.T - 1));
 #pragma unroll
   for (int q = 0; q < P; ++q) {
+    // e^{2 pi i x / M}, x = n2 k1 < M, as e^{2 pi i (x >> log B) / A} e^{2 pi i (x mod B) / M}
     const int n2 = tau + TPT * q;
-    Y[(int64_t)n2 << a.logT] = cmul(v[q], __ldg(a.twM + n2 * k1));
+    const int x = n2 * k1;
+    const float2 w = cmul(__ldg(a.twMA + (x >> a.logB)), __ldg(a.twM + (x & (a.B - 1))));
+    Y[(int64_t)n2 << a.logT] = cmul(v[q], w);
   }
 }
 

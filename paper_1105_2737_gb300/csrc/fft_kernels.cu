@@ -131,6 +131,7 @@ static cudaError_t launch_fourstep_t(int stage, const FourStepArgs& a, int64_t n
   const int len = stage == 2 ? a.A : a.B;  // stages 1 and 3 transform along k2 (length B)
   const int ncols = stage == 2 ? a.B : a.A;
   const int threads = a.C * len / P;
+  if (threads > 256) return cudaErrorInvalidValue;  // the kernels' launch bound
   const size_t smem = col_smem_bytes(len, a.C);
   const dim3 grid((unsigned)(ncols / a.C), 1, (unsigned)nfields);
   if (stage == 3) {  // stage 1 with mirror-closed columns: C / 2 column pairs per CTA

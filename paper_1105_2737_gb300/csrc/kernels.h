@@ -116,7 +116,15 @@ struct FourStepArgs {
   int64_t stab_zstride;
   const uint64_t* seed_ptr;
   float* const* zout;
+  // s_k laid out along k2 for the paired first stage: stabT[k1 B + k2] =
+  // s_{k1 + A k2} (M entries per field, stride stabT_zstride); s_M from stab
+  const float* stabT;
+  int64_t stabT_zstride;
+  const float2* tw2B;  // exp(2 pi i j / (2 B)), j < 2B
+  const float2* twMA;  // exp(2 pi i j / A) = exp(2 pi i j B / M), j < A
 };
+// stabT of a four-step plan from its s_k table (1 field).
+cudaError_t build_stab_fourstep(float* stabT, const float* stab, int A, int B, cudaStream_t s);
 // stage 1, 2, or 3 = stage 1 with mirror-closed column pairs (a.C / 2 pairs per
 // CTA, Y tile a.T = a.C / 2; each X drawn once, see fourstep1_pair_body).
 cudaError_t launch_fourstep(int stage, int P, const FourStepArgs& a, int64_t nfields, cudaStream_t s);

@@ -63,19 +63,19 @@ __global__ void __launch_bounds__(512) row_kernel_gs(RowArgs a, int64_t ntiles) 
 }
 
 template <int P>
-__global__ void __launch_bounds__(512) fourstep_stage1(FourStepArgs a) {
+__global__ void __launch_bounds__(256, 3) fourstep_stage1(FourStepArgs a) {
   extern __shared__ float2 sm[];
   fourstep1_body<P>(a, blockIdx.x, blockIdx.z, blockDim.x, sm);
 }
 
 template <int P>
-__global__ void __launch_bounds__(512) fourstep_stage1_pair(FourStepArgs a) {
+__global__ void __launch_bounds__(256, 3) fourstep_stage1_pair(FourStepArgs a) {
   extern __shared__ float2 sm[];
   fourstep1_pair_body<P>(a, blockIdx.x, blockIdx.z, blockDim.x, sm);
 }
 
 template <int P>
-__global__ void __launch_bounds__(512) fourstep_stage2(FourStepArgs a) {
+__global__ void __launch_bounds__(256, 2) fourstep_stage2(FourStepArgs a) {
   extern __shared__ float2 sm[];
   fourstep2_body<P>(a, blockIdx.x, blockIdx.z, blockDim.x, sm);
 }

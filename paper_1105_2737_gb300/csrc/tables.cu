@@ -73,6 +73,19 @@ cudaError_t build_twiddles(float2* tw, int maxlen, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+__global__ void stab_fourstep_kernel(float* stabT, const float* stab, int A, int B) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)A * B) return;
+  const int k1 = (int)(i / B), k2 = (int)(i - (int64_t)k1 * B);
+  stabT[i] = stab[k1 + (int64_t)A * k2];
+}
+
+cudaError_t build_stab_fourstep(float* stabT, const float* stab, int A, int B, cudaStream_t s) {
+  const int64_t n = (int64_t)A * B;
+  stab_fourstep_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(stabT, stab, A, B);
+  return cudaGetLastError();
+}
+
 cudaError_t build_twiddles_d(double2* tw, int maxlen, cudaStream_t s) {
   const int total = 2 * maxlen;
   twiddle_kernel_d<<<(total + 255) / 256, 256, 0, s>>>(tw, total);
