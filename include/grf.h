@@ -110,10 +110,13 @@ typedef struct grf_plan_s* grf_plan;
  *               grid goes up to 2^22 (Algorithm 2 in FP32 by a four-step c2r,
  *               and the FP64 plain form), 8192 for Algorithm 1 in FP32.  Every
  *               even 2^a 3^b 5^c 7^e is taken: FP32 plans on powers of two run
- *               the fused kernels; FP64 plans, and FP32 plans with another size
- *               on some axis, run the plain form (one launch sequence per
- *               field, radix-2, 3, 5 and 7 Stockham stages; such FP32 plans have
- *               no adjoint, rfft or tuner).
+ *               the fused kernels; FP32 2-D Algorithm 2 plans with another
+ *               size on some axis run two fused passes over the whole batch
+ *               (noise + axis-1 DFT, then c2r rows; radix-2, 3, 4, 5, 7 and 8
+ *               stages in shared memory); FP64 plans and the other FP32 plans
+ *               off powers of two run the plain form (one launch sequence per
+ *               field, radix-2, 3, 5 and 7 Stockham stages).  FP32 plans off
+ *               powers of two have no adjoint, rfft or tuner.
  *   L         : host array of d edge lengths, each > 0.
  *   spec      : host pointer to the spectral density parameters.
  *   alg       : grf_algorithm.

@@ -185,6 +185,12 @@ struct grf_plan_s {
   // (axes whose size is not a power of two; NULL otherwise)
   double2* twax64[3] = {nullptr, nullptr, nullptr};
   float2* twax32[3] = {nullptr, nullptr, nullptr};
+  // FP32 2-D Algorithm 2 plans of those sizes: the fused passes of mixed_fused.cu
+  bool mixfused = false;
+  int mixC1 = 1, mixT = 1;
+  int mixnst[2] = {0, 0};
+  int mixrad[2][16] = {};
+  float2* twMmix = nullptr;  // e^{2 pi i k / M}, k < M, when M is not a power of two
 
   // host delivery
   static constexpr int kCopyStreams = 4;
@@ -237,6 +243,7 @@ void free_plan(grf_plan p) {
     cudaFree(p->twax64[i]);
     cudaFree(p->twax32[i]);
   }
+  cudaFree(p->twMmix);
   for (int i = 0; i < 2; ++i) {
     cudaFree(p->stage[i]);
     if (p->ev_done[i]) cudaEventDestroy(p->ev_done[i]);
@@ -360,6 +367,61 @@ HalfGeom half_geom(const grf_plan_s* p, uint64_t seed, int64_t field0) {
 }
 
 const float2* twp(const grf_plan_s* p, int len) { return p->tw + len; }
+
+// Radices of a length n = 2^a 3^b 5^c 7^e for the mixed-radix stages: 8s, then a
+// 4 or a 2 for the rest of the powers of two, then 3s, 5s and 7s.  False if
+// n has another factor or needs more than 16 stages.
+bool mixed_radices(int n, int* rad, int* nst) {
+  int k = 0;
+  auto push = [&](int r) {
+    if (k < 16) rad[k] = r;
+    ++k;
+  };
+  while (n % 8 == 0) push(8), n /= 8;
+  if (n % 4 == 0) push(4), n /= 4;
+  if (n % 2 == 0) push(2), n /= 2;
+  for (int r : {3, 5, 7})
+    while (n % r == 0) push(r), n /= r;
+  *nst = k;
+  return n == 1 && k >= 1 && k <= 16;
+}
+
+// The schedule of the fused mixed-radix passes: C1 columns per CTA of pass 1
+// (C1 N1 <= 4096 entries, 16 B each in two buffers), T rows per CTA of pass 2
+// (a power of two <= 4 dividing N1, the tile within 72 KB).
+bool mixed_schedule(int N1, int M, int* C1, int* T, int (*rad)[16], int* nst) {
+  if (N1 > 4096 || M > 4096 || N1 < 2 || M < 1) return false;
+  if (!mixed_radices(N1, rad[0], &nst[0]) || !mixed_radices(M, rad[1], &nst[1])) return false;
+  int c = 4096 / N1;
+  if (c > M + 1) c = M + 1;
+  *C1 = c < 1 ? 1 : c;
+  int t = 4;
+  while (t > 1 && (N1 % t || mixed_c2r_smem_bytes(M, t) > 72 * 1024)) t >>= 1;
+  *T = t;
+  return true;
+}
+
+MixedArgs mixed_args(const grf_plan_s* p, uint64_t seed, float* out) {
+  MixedArgs a{};
+  a.N1 = p->N1;
+  a.M = p->M;
+  a.T = p->mixT;
+  a.C1 = p->mixC1;
+  a.nst1 = p->mixnst[0];
+  a.nst2 = p->mixnst[1];
+  for (int i = 0; i < 16; ++i) {
+    a.rad1[i] = p->mixrad[0][i];
+    a.rad2[i] = p->mixrad[1][i];
+  }
+  a.tw1 = p->twax32[0] ? p->twax32[0] : twp(p, p->N1);
+  a.tw2 = p->twax32[1] ? p->twax32[1] : twp(p, 2 * p->M);
+  a.twM = p->twMmix ? p->twMmix : twp(p, p->M);
+  a.g = half_geom(p, seed, 0);
+  a.ws = p->ws;
+  a.ws_stride = p->ws_field;
+  a.out = out;
+  return a;
+}
 
 // Column pass along axis 1 (the transform length N1); plane = whole field.
 ColArgs col_axis1(const grf_plan_s* p, const HalfGeom& g, const float2* in, float2* out, int T) {
@@ -825,14 +887,26 @@ grf_status grf_plan_create(grf_plan* out, int d, const int64_t* n, const double*
     PLAN_CUDA(build_twiddles(p->tw, (int)maxlen, s), "twiddle build");
     PLAN_CUDA(dmalloc(&p->stab, p->fold_size), "s table");
     PLAN_CUDA(build_stab(p->stab, nullptr, sp, 0.0, s), "s table build");
-    PLAN_CUDA(dmalloc(&p->buf32A, p->ntot), "FP32 plain buffer");
-    PLAN_CUDA(dmalloc(&p->buf32B, p->ntot), "FP32 plain buffer");
     for (int i = 0; i < d; ++i)
       if (!is_pow2(n[i])) {
         PLAN_CUDA(dmalloc(&p->twax32[i], n[i]), "axis twiddles");
         PLAN_CUDA(build_axis_twiddles(p->twax32[i], (int)n[i], s), "axis twiddles");
       }
     p->chunk = max_batch;
+    const char* mf = std::getenv("GRF_MIXED_FUSED");  // "0": keep the plain form
+    p->mixfused = d == 2 && alg == GRF_ALG_ONE_FFT && !(mf && mf[0] == '0') &&
+                  mixed_schedule(p->N1, p->M, &p->mixC1, &p->mixT, p->mixrad, p->mixnst);
+    if (p->mixfused) {
+      if (!is_pow2(p->M)) {
+        PLAN_CUDA(dmalloc(&p->twMmix, p->M), "axis twiddles");
+        PLAN_CUDA(build_axis_twiddles(p->twMmix, p->M, s), "axis twiddles");
+      }
+      p->ws_field = p->hsize;
+      PLAN_CUDA(dmalloc(&p->ws, (size_t)(p->chunk * p->ws_field)), "workspace");
+    } else {
+      PLAN_CUDA(dmalloc(&p->buf32A, p->ntot), "FP32 plain buffer");
+      PLAN_CUDA(dmalloc(&p->buf32B, p->ntot), "FP32 plain buffer");
+    }
   } else if (prec == GRF_FP32) {
     PLAN_CUDA(dmalloc(&p->tw, 2 * maxlen + kStageTableEntries), "twiddle table");
     PLAN_CUDA(build_twiddles(p->tw, (int)maxlen, s), "twiddle build");
@@ -942,6 +1016,12 @@ grf_status grf_sample(grf_plan p, uint64_t seed, int64_t batch, void* out, void*
   if (!out) return fail(GRF_ERR_INVALID_ARG, "out is NULL");
   if (batch < 1 || batch > p->max_batch) return fail(GRF_ERR_INVALID_ARG, "batch must be in [1, max_batch]");
   cudaStream_t s = (cudaStream_t)stream;
+  if (p->mixfused) {
+    const MixedArgs a = mixed_args(p, seed, (float*)out);
+    TLAUNCH(GRF_KERNEL_NOISE_COLUMNS, launch_mixed_noise(a, batch, s), "mixed-radix noise pass");
+    TLAUNCH(GRF_KERNEL_ROWS_C2R, launch_mixed_c2r(a, batch, s), "mixed-radix c2r pass");
+    return GRF_OK;
+  }
   if (p->prec == GRF_FP64 || p->mixed) {
     Plain64Geom g{};
     g.d = p->d;

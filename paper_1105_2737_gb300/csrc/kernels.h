@@ -185,6 +185,30 @@ size_t plane3_ws_entries(int N1, int N2, int M);  // per field
 cudaError_t launch_plane3_noise(const ColArgs& a, const PlaneArgs& pl, int64_t nfields, cudaStream_t s);
 cudaError_t launch_plane3_c2r(const PlaneArgs& pl, int64_t nfields, cudaStream_t s);
 
+// The fused passes of FP32 2-D plans of sizes 2^a 3^b 5^c 7^d (mixed_fused.cu),
+// Algorithm 2: pass 1 (noise + the axis-1 inverse DFT of C1 columns per CTA,
+// in shared memory) writes X to ws [j1 / T][kd][j1 % T]; pass 2 (one tile of
+// T rows per CTA) forms the c2r split and the M-point inverse DFT.  Radix lists
+// rad1 (length N1) and rad2 (length M) take radices 2, 3, 4, 5, 7, 8.
+struct MixedArgs {
+  int N1, M;
+  int T, C1;
+  int nst1, nst2;
+  int rad1[16], rad2[16];
+  const float2* tw1;   // e^{2 pi i k / N1}, k < N1
+  const float2* tw2;   // e^{2 pi i k / N2}, k < N2
+  const float2* twM;   // e^{2 pi i k / M}, k < M
+  HalfGeom g;          // noise keys and the folded s_K table
+  float2* ws;
+  int64_t ws_stride;   // entries per field (N1 (M + 1))
+  float* out;
+  float* const* zout;  // batch plans: output of the field at launch index z (NULL: out)
+};
+size_t mixed_noise_smem_bytes(int N1, int C1);
+size_t mixed_c2r_smem_bytes(int M, int T);
+cudaError_t launch_mixed_noise(const MixedArgs& a, int64_t nfields, cudaStream_t s);
+cudaError_t launch_mixed_c2r(const MixedArgs& a, int64_t nfields, cudaStream_t s);
+
 // Host launchers (fft_kernels.cu).  P is the points per thread of the
 // transform (16 if the length is >= 16, else the length itself).
 cudaError_t launch_col(int src, int mode, int P, const ColArgs& a, dim3 grid, cudaStream_t s);

@@ -1,0 +1,128 @@
+// Fused passes of FP32 2-D plans whose sizes are 2^a 3^b 5^c 7^d (Algorithm
+// 2): the same two passes as the power-of-two path, with the mixed-radix
+// Stockham stages of mixed_fused.cuh run in shared memory.
+//   pass 1: a CTA takes C1 columns kd of the half spectrum: draws the noise of
+//           their N1 entries (rows k1 and k1 + N1/2 share a Philox call; the
+//           planes kd in {0, M} take the conjugation rule), scales by s_K,
+//           runs the inverse DFT of length N1 and writes X to the workspace
+//           [j1 / T][kd][j1 % T];
+//   pass 2: a CTA takes one tile of T rows j1: reads its (M + 1) T entries
+//           (one contiguous run), forms the c2r split
+//           Z[k] = (X[k] + conj X[M-k]) + i e^{2 pi i k / N2} (X[k] - conj X[M-k]),
+//           runs the inverse DFT of length M and writes the N2 reals of each row.
+#include "mixed_fused.cuh"
+#include "bodies.cuh"
+
+namespace grf {
+
+namespace {
+
+constexpr int kMixedThreads = 256;
+
+__global__ void __launch_bounds__(kMixedThreads) mixed_noise_kernel(MixedArgs a) {
+  extern __shared__ float2 sm[];
+  const int N1 = a.N1, M = a.M, H = N1 / 2, C = a.C1;
+  float2* bufA = sm;
+  float2* bufB = sm + (size_t)C * N1;
+  const HalfGeom& g = a.g;
+  const int64_t field = blockIdx.z;
+  const uint64_t key = field_key(g, field);
+  const float* stab = field_stab(g, field);
+  const int kd0 = blockIdx.x * C;
+  const int t = threadIdx.x, nthr = blockDim.x;
+  const float r2 = 0.70710678118654752440f;
+  // noise x s_K into bufA[c N1 + k1]
+  for (int idx = t; idx < C * H; idx += nthr) {
+    const int c = idx / H, i = idx - c * H;
+    const int kd = kd0 + c;
+    float2 x0 = make_float2(0.f, 0.f), x1 = make_float2(0.f, 0.f);
+    if (kd <= M) {
+      const float* srow = stab + (size_t)kd * (N1 / 2 + 1);
+      const float s0 = __ldg(srow + i), s1 = __ldg(srow + (H - i));  // folded |k1|: i and N1 - (i + H)
+      if (kd != 0 && kd != M) {  // rows i and i + H share one call
+        const u32x4 w = philox_call((uint64_t)i * (uint64_t)(M + 1) + (uint64_t)kd, 0u, key);
+        x0 = cscale(box_muller(w.x, w.y, g.trig), s0 * r2);
+        x1 = cscale(box_muller(w.z, w.w, g.trig), s1 * r2);
+      } else {
+        x0 = cscale(alg2_xi_grid(i, 0, kd, N1, 1, M, key, g.trig), s0);
+        x1 = cscale(alg2_xi_grid(i + H, 0, kd, N1, 1, M, key, g.trig), s1);
+      }
+    }
+    bufA[(size_t)c * N1 + i] = x0;
+    bufA[(size_t)c * N1 + i + H] = x1;
+  }
+  const float2* X = mixed_transform(bufA, bufB, N1, N1, C, a.rad1, a.nst1, a.tw1);
+  // X to the workspace tile layout, (j1 mod T) fastest, then the column
+  const int T = a.T;
+  float2* ws = a.ws + field * a.ws_stride;
+  const int64_t ncols = M + 1;
+  for (int idx = t; idx < C * N1; idx += nthr) {
+    const int r = idx % T;
+    const int rest = idx / T;
+    const int c = rest % C, jt = rest / C;
+    const int kd = kd0 + c;
+    if (kd > M) continue;
+    const int j1 = jt * T + r;
+    ws[((int64_t)jt * ncols + kd) * T + r] = X[(size_t)c * N1 + j1];
+  }
+}
+
+__global__ void __launch_bounds__(kMixedThreads) mixed_c2r_kernel(MixedArgs a) {
+  extern __shared__ float2 sm[];
+  const int M = a.M, T = a.T;
+  const int64_t ncols = M + 1;
+  float2* bufA = sm;                          // T x (M + 1): X, then a stage buffer
+  float2* bufB = sm + (size_t)T * (M + 1);    // T x M
+  const int64_t field = blockIdx.z;
+  const int jt = blockIdx.x;
+  const int t = threadIdx.x, nthr = blockDim.x;
+  const float2* ws = a.ws + field * a.ws_stride + (int64_t)jt * ncols * T;
+  // the tile's contiguous run [kd][r] -> bufA[r (M + 1) + kd]
+  for (int idx = t; idx < (int)ncols * T; idx += nthr) {
+    const int r = idx % T, kd = idx / T;
+    bufA[(size_t)r * (M + 1) + kd] = __ldcg(ws + idx);
+  }
+  __syncthreads();
+  // Z of the c2r split -> bufB[r M + k]
+  for (int idx = t; idx < M * T; idx += nthr) {
+    const int r = idx / M, k = idx - r * M;
+    const float2* x = bufA + (size_t)r * (M + 1);
+    bufB[(size_t)r * M + k] = c2r_pre(x[k], x[M - k], __ldg(a.tw2 + k));
+  }
+  // the M-point inverse DFT (twiddles from twM, e^{2 pi i k / M})
+  const float2* z = mixed_transform(bufB, bufA, M, M, T, a.rad2, a.nst2, a.twM);
+  // f[2m] + i f[2m + 1] = z[m]
+  for (int idx = t; idx < M * T; idx += nthr) {
+    const int r = idx / M, m = idx - r * M;
+    const int64_t j1 = (int64_t)jt * T + r;
+    float* row = a.zout ? a.zout[field] + j1 * (2 * M) : a.out + (field * a.N1 + j1) * (2 * M);
+    reinterpret_cast<float2*>(row)[m] = z[(size_t)r * M + m];
+  }
+}
+
+}  // namespace
+
+size_t mixed_noise_smem_bytes(int N1, int C1) { return (size_t)2 * C1 * N1 * sizeof(float2); }
+size_t mixed_c2r_smem_bytes(int M, int T) { return (size_t)T * (2 * M + 1) * sizeof(float2); }
+
+cudaError_t launch_mixed_noise(const MixedArgs& a, int64_t nfields, cudaStream_t s) {
+  if (a.C1 < 1 || a.T < 1 || a.nst1 < 1 || a.nst1 > 16 || nfields < 1 || nfields > 65535 || a.N1 % a.T)
+    return cudaErrorInvalidValue;
+  const size_t smem = mixed_noise_smem_bytes(a.N1, a.C1);
+  cudaError_t e = prepare_kernel((const void*)mixed_noise_kernel, kMixedThreads, smem);
+  if (e != cudaSuccess) return e;
+  mixed_noise_kernel<<<dim3((unsigned)((a.M + 1 + a.C1 - 1) / a.C1), 1, (unsigned)nfields), kMixedThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mixed_c2r(const MixedArgs& a, int64_t nfields, cudaStream_t s) {
+  if (a.T < 1 || a.nst2 < 1 || a.nst2 > 16 || nfields < 1 || nfields > 65535 || a.N1 % a.T)
+    return cudaErrorInvalidValue;
+  const size_t smem = mixed_c2r_smem_bytes(a.M, a.T);
+  cudaError_t e = prepare_kernel((const void*)mixed_c2r_kernel, kMixedThreads, smem);
+  if (e != cudaSuccess) return e;
+  mixed_c2r_kernel<<<dim3((unsigned)(a.N1 / a.T), 1, (unsigned)nfields), kMixedThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace grf

@@ -186,6 +186,42 @@ def test_fp32_mixed_radix_full_size_3000sq():
     g.close()
 
 
+# FP32 2-D Algorithm 2 off powers of two: the fused mixed-radix passes.  Cases
+# with several column CTAs and a ragged last one ((M + 1) mod C1 != 0), radix 7
+# on either axis, a power-of-two axis beside a mixed one, N1 = 2, and the
+# largest last axis (M = 4096).
+FUSED = [((2, 6), "matern"), ((1000, 210), "matern"), ((448, 252), "gaussian"), ((14, 8192), "matern"),
+         ((4096, 3000), "matern"), ((3000, 4096), "paper_poly"), ((96, 80), "matern"), ((6, 2), "matern")]
+
+
+@pytest.mark.parametrize("case", range(len(FUSED)))
+def test_fp32_mixed_fused_passes(case):
+    """The fields of a batch of 3 against the oracle (the last one alone on the
+    12 M-point grids); the plan runs the two
+    fused passes per call (timing records), not the per-field plain form."""
+    from paper_1105_2737_gb300 import _lib as L
+    n, fam = FUSED[case]
+    kw = dict(ell=0.05, nu=1.5) if fam != "paper_poly" else dict(m=2.0, k=1, l=2, n=1)
+    Lb = (1.0, 1.5)
+    g = _api().GRF(n, Lb, family=fam, precision="fp32", max_batch=3, **kw)
+    L.grf_plan_timing(g.handle, 16)
+    f = g.sample(seed=77, batch=3).cpu().numpy()
+    _, recs = L.grf_plan_timing_read(g.handle)
+    L.grf_plan_timing(g.handle, 0)
+    kinds = [k for k, _ in recs]
+    if n[1] // 2 > 1:  # the fused schedule needs M >= 2
+        assert kinds == ["noise_columns", "rows_c2r"], kinds
+    else:
+        assert set(kinds) == {"plain64"}, kinds
+    sig = None
+    for b in (range(3) if n[0] * n[1] < 4_000_000 else (2,)):  # the oracle takes ~10 s per 12 M-point field
+        ref = O.alg2_field(n, Lb, _ospec(fam, **kw), 77 + b)
+        if fam == "paper_poly":
+            sig = float(np.sqrt((ref ** 2).mean()))
+        _compare(f[b], ref, sigma=1.0 if sig is None else sig)
+    g.close()
+
+
 def test_fp32_mixed_plan_has_no_adjoint_or_rfft():
     from paper_1105_2737_gb300 import _lib as L
     g = _api().GRF((12, 20), (1.0, 1.0), precision="fp32", max_batch=1)
