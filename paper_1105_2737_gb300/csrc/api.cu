@@ -187,10 +187,10 @@ struct grf_plan_s {
   float2* twax32[3] = {nullptr, nullptr, nullptr};
   // FP32 2-D Algorithm 2 plans of those sizes: the fused passes of mixed_fused.cu
   bool mixfused = false;
-  int mixC1 = 1, mixT = 1;
+  int mixC1 = 1, mixlogT = 0, mixthreads2 = 256;
   int mixnst[2] = {0, 0};
   int mixrad[2][16] = {};
-  float2* twMmix = nullptr;  // e^{2 pi i k / M}, k < M, when M is not a power of two
+  float2* mixtab[2] = {nullptr, nullptr};  // stage tables of N1 and M
 
   // host delivery
   static constexpr int kCopyStreams = 4;
@@ -243,7 +243,8 @@ void free_plan(grf_plan p) {
     cudaFree(p->twax64[i]);
     cudaFree(p->twax32[i]);
   }
-  cudaFree(p->twMmix);
+  cudaFree(p->mixtab[0]);
+  cudaFree(p->mixtab[1]);
   for (int i = 0; i < 2; ++i) {
     cudaFree(p->stage[i]);
     if (p->ev_done[i]) cudaEventDestroy(p->ev_done[i]);
@@ -368,36 +369,45 @@ HalfGeom half_geom(const grf_plan_s* p, uint64_t seed, int64_t field0) {
 
 const float2* twp(const grf_plan_s* p, int len) { return p->tw + len; }
 
-// Radices of a length n = 2^a 3^b 5^c 7^e for the mixed-radix stages: 8s, then a
-// 4 or a 2 for the rest of the powers of two, then 3s, 5s and 7s.  False if
-// n has another factor or needs more than 16 stages.
+// Radices of a length n = 2^a 3^b 5^c 7^e for the mixed-radix stages: the odd
+// ones first (the first stage writes at a stride of its radix, which an odd
+// radix spreads over all shared-memory banks), then 8s and a 4 or a 2 for the
+// rest of the powers of two.  False if n has another factor or needs more
+// than 16 stages.
 bool mixed_radices(int n, int* rad, int* nst) {
   int k = 0;
   auto push = [&](int r) {
     if (k < 16) rad[k] = r;
     ++k;
   };
+  for (int r : {3, 5, 7})
+    while (n % r == 0) push(r), n /= r;
   while (n % 8 == 0) push(8), n /= 8;
   if (n % 4 == 0) push(4), n /= 4;
   if (n % 2 == 0) push(2), n /= 2;
-  for (int r : {3, 5, 7})
-    while (n % r == 0) push(r), n /= r;
   *nst = k;
   return n == 1 && k >= 1 && k <= 16;
 }
 
 // The schedule of the fused mixed-radix passes: C1 columns per CTA of pass 1
-// (C1 N1 <= 4096 entries, 16 B each in two buffers), T rows per CTA of pass 2
-// (a power of two <= 4 dividing N1, the tile within 72 KB).
-bool mixed_schedule(int N1, int M, int* C1, int* T, int (*rad)[16], int* nst) {
-  if (N1 > 4096 || M > 4096 || N1 < 2 || M < 1) return false;
+// (C1 N1 <= 4096 entries, 16 B each in two buffers); pass 2 takes T = 2^logT
+// rows per CTA, the largest T <= 4 dividing N1 whose tile fits in 48 KB (four
+// CTAs of 256 threads per SM; measured at 3000^2, 1000^2 and 3000 x 4096 against
+// the neighbouring T and 512 threads).  GRF_MIXED_T and GRF_MIXED_THREADS
+// override T and the threads of pass 2.
+bool mixed_schedule(int N1, int M, int* C1, int* logT, int* threads2, int (*rad)[16], int* nst) {
+  if (N1 > 4096 || M > 4096 || N1 < 2 || M < 2) return false;
   if (!mixed_radices(N1, rad[0], &nst[0]) || !mixed_radices(M, rad[1], &nst[1])) return false;
   int c = 4096 / N1;
   if (c > M + 1) c = M + 1;
   *C1 = c < 1 ? 1 : c;
   int t = 4;
-  while (t > 1 && (N1 % t || mixed_c2r_smem_bytes(M, t) > 72 * 1024)) t >>= 1;
-  *T = t;
+  if (const char* te = std::getenv("GRF_MIXED_T")) t = std::max(1, std::min(8, std::atoi(te)));
+  const bool forced = std::getenv("GRF_MIXED_T") != nullptr;
+  while (t > 1 && (N1 % t || (t & (t - 1)) || mixed_c2r_smem_bytes(M, t) > (forced ? 200 : 48) * 1024 + 64)) t >>= 1;
+  *logT = t == 8 ? 3 : t == 4 ? 2 : t == 2 ? 1 : 0;
+  *threads2 = 256;
+  if (const char* th = std::getenv("GRF_MIXED_THREADS")) *threads2 = std::atoi(th) == 512 ? 512 : 256;
   return true;
 }
 
@@ -405,7 +415,8 @@ MixedArgs mixed_args(const grf_plan_s* p, uint64_t seed, float* out) {
   MixedArgs a{};
   a.N1 = p->N1;
   a.M = p->M;
-  a.T = p->mixT;
+  a.logT = p->mixlogT;
+  a.threads2 = p->mixthreads2;
   a.C1 = p->mixC1;
   a.nst1 = p->mixnst[0];
   a.nst2 = p->mixnst[1];
@@ -413,9 +424,9 @@ MixedArgs mixed_args(const grf_plan_s* p, uint64_t seed, float* out) {
     a.rad1[i] = p->mixrad[0][i];
     a.rad2[i] = p->mixrad[1][i];
   }
-  a.tw1 = p->twax32[0] ? p->twax32[0] : twp(p, p->N1);
+  a.st1 = p->mixtab[0];
+  a.st2 = p->mixtab[1];
   a.tw2 = p->twax32[1] ? p->twax32[1] : twp(p, 2 * p->M);
-  a.twM = p->twMmix ? p->twMmix : twp(p, p->M);
   a.g = half_geom(p, seed, 0);
   a.ws = p->ws;
   a.ws_stride = p->ws_field;
@@ -895,11 +906,11 @@ grf_status grf_plan_create(grf_plan* out, int d, const int64_t* n, const double*
     p->chunk = max_batch;
     const char* mf = std::getenv("GRF_MIXED_FUSED");  // "0": keep the plain form
     p->mixfused = d == 2 && alg == GRF_ALG_ONE_FFT && !(mf && mf[0] == '0') &&
-                  mixed_schedule(p->N1, p->M, &p->mixC1, &p->mixT, p->mixrad, p->mixnst);
+                  mixed_schedule(p->N1, p->M, &p->mixC1, &p->mixlogT, &p->mixthreads2, p->mixrad, p->mixnst);
     if (p->mixfused) {
-      if (!is_pow2(p->M)) {
-        PLAN_CUDA(dmalloc(&p->twMmix, p->M), "axis twiddles");
-        PLAN_CUDA(build_axis_twiddles(p->twMmix, p->M, s), "axis twiddles");
+      for (int i = 0; i < 2; ++i) {
+        PLAN_CUDA(dmalloc(&p->mixtab[i], i == 0 ? p->N1 : p->M), "stage table");
+        PLAN_CUDA(build_mixed_stage_table(p->mixtab[i], p->mixrad[i], p->mixnst[i], s), "stage table");
       }
       p->ws_field = p->hsize;
       PLAN_CUDA(dmalloc(&p->ws, (size_t)(p->chunk * p->ws_field)), "workspace");

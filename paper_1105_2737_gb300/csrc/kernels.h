@@ -192,18 +192,22 @@ cudaError_t launch_plane3_c2r(const PlaneArgs& pl, int64_t nfields, cudaStream_t
 // rad1 (length N1) and rad2 (length M) take radices 2, 3, 4, 5, 7, 8.
 struct MixedArgs {
   int N1, M;
-  int T, C1;
+  int logT, C1;        // workspace tile T = 2^logT rows (T divides N1); columns per CTA of pass 1
+  int threads2;        // threads per CTA of pass 2 (256 or 512)
   int nst1, nst2;
   int rad1[16], rad2[16];
-  const float2* tw1;   // e^{2 pi i k / N1}, k < N1
+  const float2* st1;   // stage tables of the lengths N1 and M (build_mixed_stage_table)
+  const float2* st2;
   const float2* tw2;   // e^{2 pi i k / N2}, k < N2
-  const float2* twM;   // e^{2 pi i k / M}, k < M
   HalfGeom g;          // noise keys and the folded s_K table
   float2* ws;
   int64_t ws_stride;   // entries per field (N1 (M + 1))
   float* out;
   float* const* zout;  // batch plans: output of the field at launch index z (NULL: out)
 };
+// The stage table of a length N with radices radix[0..nst): N - 1 entries,
+// stage s (span Ns) at Ns - 1: e^{2 pi i m r / (R Ns)} at (r - 1) Ns + m.
+cudaError_t build_mixed_stage_table(float2* tab, const int* radix, int nst, cudaStream_t s);
 size_t mixed_noise_smem_bytes(int N1, int C1);
 size_t mixed_c2r_smem_bytes(int M, int T);
 cudaError_t launch_mixed_noise(const MixedArgs& a, int64_t nfields, cudaStream_t s);

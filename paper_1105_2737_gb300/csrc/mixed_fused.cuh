@@ -6,7 +6,7 @@
 // e^{2 pi i (j mod Ns) r / (R Ns)}, takes the inverse DFT of R points and writes
 // position (j - j mod Ns) R + j mod Ns + r Ns (Stockham autosort: after the
 // last stage the sequence is in natural order, whatever the order of radices).
-// Twiddles come from the sequence's table tw[k] = e^{2 pi i k / N} (FP64-built).
+// Twiddles come from a per-length stage table (FP64-built, mixed_fused.cu).
 #pragma once
 #include "fft_core.cuh"
 
@@ -66,27 +66,37 @@ GRF_DEV void dft_small(float2 (&x)[R]) {
   else dft_odd<R>(x);
 }
 
+// floor(n / d) for 0 <= n < 2^22 from rd = the correctly rounded 1 / d: the
+// product (n + 1/2) rd is within 2^-23 (n + 1/2) / d of (n + 1/2) / d, less
+// than the 1 / (2d) that separates (n + 1/2) / d from the nearest integer.
+GRF_DEV int qdiv(int n, float rd) { return __float2int_rz(((float)n + 0.5f) * rd); }
+
 // One stage over C sequences of length N (sequence c at src + c * pitch), by
-// the nthr threads t < nthr; the caller synchronises around it.
+// the nthr threads t < nthr; the caller synchronises around it.  The stage's
+// twiddles e^{2 pi i m r / (R Ns)} sit at tab[Ns - 1 + (r - 1) Ns + m]: lanes
+// with consecutive m read consecutive entries.
 template <int R>
-GRF_DEV void mixed_stage(const float2* src, float2* dst, int pitch, int N, int Ns, int C,
-                         const float2* __restrict__ tw, int t, int nthr) {
+GRF_DEV void mixed_stage(const float2* __restrict__ src, float2* __restrict__ dst, int pitch, int N, int Ns, int C,
+                         const float2* __restrict__ tab, int t, int nthr) {
   const int nb = N / R;
-  const int tstep = N / (R * Ns);  // e^{2 pi i m r / (R Ns)} = tw[m r tstep]
+  const float rnb = __frcp_rn((float)nb), rNs = __frcp_rn((float)Ns);
   for (int idx = t; idx < C * nb; idx += nthr) {
-    const int c = idx / nb, j = idx - c * nb;
-    const float2* s = src + (size_t)c * pitch;
-    float2* d = dst + (size_t)c * pitch;
-    const int m = j % Ns;
+    const int c = C == 1 ? 0 : qdiv(idx, rnb);
+    const int j = idx - c * nb;
+    const int q = qdiv(j, rNs);
+    const int m = j - q * Ns;
+    const float2* s = src + c * pitch;
+    float2* d = dst + c * pitch;
     float2 x[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) x[r] = s[j + r * nb];
     if (Ns > 1) {
+      const float2* w = tab + (Ns - 1) + m;
 #pragma unroll
-      for (int r = 1; r < R; ++r) x[r] = cmul(x[r], __ldg(tw + m * r * tstep));
+      for (int r = 1; r < R; ++r) x[r] = cmul(x[r], __ldg(w + (r - 1) * Ns));
     }
     dft_small<R>(x);
-    const int base = (j - m) * R + m;
+    const int base = q * Ns * R + m;
 #pragma unroll
     for (int r = 0; r < R; ++r) d[base + r * Ns] = x[r];
   }
@@ -94,21 +104,21 @@ GRF_DEV void mixed_stage(const float2* src, float2* dst, int pitch, int N, int N
 
 // All stages of the inverse DFT of C sequences of length N held in buffer a
 // (pitch `pitch`), ping-ponging with buffer b; returns the buffer that holds
-// the result.  radix[0..nst) multiply to N.  Starts and ends with a barrier
-// over the whole CTA.
+// the result.  radix[0..nst) multiply to N; tab is the length's stage table.
+// Starts and ends with a barrier over the whole CTA.
 GRF_DEV float2* mixed_transform(float2* a, float2* b, int pitch, int N, int C, const int* radix, int nst,
-                                const float2* __restrict__ tw) {
+                                const float2* __restrict__ tab) {
   const int t = threadIdx.x, nthr = blockDim.x;
   int Ns = 1;
   for (int st = 0; st < nst; ++st) {
     __syncthreads();
     switch (radix[st]) {
-      case 2: mixed_stage<2>(a, b, pitch, N, Ns, C, tw, t, nthr); break;
-      case 3: mixed_stage<3>(a, b, pitch, N, Ns, C, tw, t, nthr); break;
-      case 4: mixed_stage<4>(a, b, pitch, N, Ns, C, tw, t, nthr); break;
-      case 5: mixed_stage<5>(a, b, pitch, N, Ns, C, tw, t, nthr); break;
-      case 7: mixed_stage<7>(a, b, pitch, N, Ns, C, tw, t, nthr); break;
-      default: mixed_stage<8>(a, b, pitch, N, Ns, C, tw, t, nthr); break;
+      case 2: mixed_stage<2>(a, b, pitch, N, Ns, C, tab, t, nthr); break;
+      case 3: mixed_stage<3>(a, b, pitch, N, Ns, C, tab, t, nthr); break;
+      case 4: mixed_stage<4>(a, b, pitch, N, Ns, C, tab, t, nthr); break;
+      case 5: mixed_stage<5>(a, b, pitch, N, Ns, C, tab, t, nthr); break;
+      case 7: mixed_stage<7>(a, b, pitch, N, Ns, C, tab, t, nthr); break;
+      default: mixed_stage<8>(a, b, pitch, N, Ns, C, tab, t, nthr); break;
     }
     Ns *= radix[st];
     float2* x = a;
