@@ -122,9 +122,9 @@ __global__ void __launch_bounds__(kR2rThreads, kR2rMinBlocks) r2r_line_kernel(R2
       tile[e] = (base >= 0 && base < kFaceLine) ? __ldcg(a.f + base + n) : 0.f;
     }
   } else {  // strided axis: neighbouring lines are neighbours in memory;
-            // eight loads in flight per thread before they go to the tile
+            // sixteen loads in flight per thread before they go to the tile
     const int E = W * G;
-    constexpr int U = 8;
+    constexpr int U = 16;
     for (int e0 = t; e0 < E; e0 += U * nthr) {
       float x[U];
 #pragma unroll
