@@ -292,8 +292,8 @@ def run_ours(args):
             with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
                 tr = json.load(f)
             ent = tr.get(kind)
-            from paper_1105_2737_gb300.build import _fingerprint
-            if ent and ent.get("fingerprint") == _fingerprint()[:16]:
+            from paper_1105_2737_gb300.build import kernel_fingerprint
+            if ent and ent.get("fingerprint") == kernel_fingerprint(kind)[:16]:
                 return float(ent["bytes_per_field"]) * BATCH
         except Exception:
             pass

@@ -52,6 +52,29 @@ def _fingerprint() -> str:
     return h.hexdigest()
 
 
+# The sources behind each kernel kind of the 2-D Algorithm 2 step (its .cu
+# files and the launch code in api.cu; every header counts too): a stored
+# DRAM-traffic figure is valid while their fingerprint is unchanged.
+KERNEL_SOURCES = {
+    "noise_columns": ("api.cu", "fft_kernels.cu", "spec_noise.cu", "noise_fast.cu", "noise_kernels.cu"),
+    "rows_c2r": ("api.cu", "fft_kernels.cu", "spec_other.cu", "c2r_tma.cu"),
+}
+
+
+def kernel_fingerprint(kind: str) -> str:
+    h = hashlib.sha256()
+    h.update(platform.machine().encode())
+    h.update(" ".join(ARCH + [f for f in NVCC_FLAGS if not f.startswith("-I")]).encode())
+    own = KERNEL_SOURCES[kind]
+    for d in (CSRC, INCLUDE):
+        for f in sorted(os.listdir(d)):
+            if f.endswith((".cuh", ".h")) or f in own:
+                with open(os.path.join(d, f), "rb") as fh:
+                    h.update(f.encode())
+                    h.update(fh.read())
+    return h.hexdigest()
+
+
 def up_to_date() -> bool:
     if not (os.path.exists(LIB) and os.path.exists(STAMP)):
         return False
