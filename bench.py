@@ -706,6 +706,25 @@ def run_mixed_study(args):
     print(json.dumps({"study": "grid sizes 2^a 3^b 5^c 7^e", "rows": rows}), flush=True)
 
 
+def run_case(args):
+    """Two calls of one small workload for an ncu capture (no timing, no JSON line)."""
+    import torch
+    from paper_1105_2737_gb300 import build
+    build()
+    from paper_1105_2737_gb300.api import GRF
+    b = args.batch if args.batch != BATCH else 2
+    if args.case == "3d256":
+        g = GRF((256, 256, 256), (1.0, 1.0, 1.0), family="gaussian", sigma=1.0, ell=0.03, max_batch=b)
+    else:
+        g = GRF((3000, 3000), (1.0, 1.0), max_batch=b, **SPEC)
+    o = g.empty(b)
+    g.sample(0, b, o)
+    g.sample(b, b, o)
+    torch.cuda.synchronize()
+    print("case %s, %d fields per call: ok" % (args.case, b), flush=True)
+    g.close()
+
+
 def run_bc_study(args):
     """Neumann / Dirichlet fields (the cosine / sine transform variant): fields/s,
     Gpts/s and the HBM roofline of each pass at 2-D 4096^2 intervals (4097^2
@@ -802,6 +821,9 @@ def main():
     ap.add_argument("--study", choices=["cov1d", "bc", "fig3", "mixed"],
                     help="run the paper's 1-D covariance study, or the Neumann / Dirichlet fields, instead")
     ap.add_argument("--study-samples", type=int, default=100_000_000)
+    ap.add_argument("--case", choices=["3d256", "mixed3000"],
+                    help="profiling: two calls of --batch fields of one workload (3-D 256^3 Gaussian ell = 0.03, "
+                         "or 2-D 3000^2 on the fused mixed-radix passes), no timing")
     args = ap.parse_args()
     if args.study == "cov1d":
         run_cov1d_study(args)
@@ -811,6 +833,8 @@ def main():
         run_fig3_study(args)
     elif args.study == "mixed":
         run_mixed_study(args)
+    elif args.case:
+        run_case(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
