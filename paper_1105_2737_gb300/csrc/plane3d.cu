@@ -55,11 +55,15 @@ GRF_DEV void plane3_subplane(const PlaneArgs& pl, float2* sub, float2* xb, int64
   constexpr int RB = CR < Q ? CR : Q;        // rows per batch that exist
   static_assert(Q % CR == 0 || CR > Q, "whole row batches");
   const int t = threadIdx.x;
-  // axis 2: inverse FFTs of length Q along k' of the columns k3 = 0..M, in place
-  // (M + 1 is odd: the full batches leave a remainder of columns, which runs
-  // on the fewest whole warps that hold it, the other warps going ahead)
+  // axis 2: inverse FFTs of length Q along k' of the columns k3 = 0..M, in
+  // place.  The planes k3 = 0 and k3 = M are Hermitian in (k1, k2), so after
+  // axis 1 each of their columns has a real inverse DFT along k2 (and so along
+  // k' for every residue s): they share one transform as X[k', 0] + i X[k', M]
+  // (real part: column 0, imaginary part: column M).  That leaves M columns,
+  // a whole number of batches when CB divides M; a remainder runs on the
+  // fewest whole warps that hold it, the other warps going ahead.
   const float2* twQ = pl.tw + Q;
-  constexpr int FULL = (M + 1) / CB, REM = (M + 1) - FULL * CB;
+  constexpr int FULL = M / CB, REM = M - FULL * CB;
   // columns of the last call: a power of two >= REM whose threads fill whole warps
   constexpr int CREM = pow2_at_least(REM > 32 / TPC ? REM : 32 / TPC) < CB ? pow2_at_least(REM > 32 / TPC ? REM : 32 / TPC) : CB;
   static_assert((CREM & (CREM - 1)) == 0 && (CREM * TPC) % 32 == 0, "whole warps");
@@ -71,15 +75,31 @@ GRF_DEV void plane3_subplane(const PlaneArgs& pl, float2* sub, float2* xb, int64
       if (REM == 0 || t >= nthr) break;
     }
     const int c = t % C, tau = t / C;
-    const int col = bi * CB + c;
-    const bool valid = col <= M;
+    const int col = bi * CB + c;  // column 0 carries the planes k3 = 0 and k3 = M
+    const bool valid = col < M;
     float2 v[P];
 #pragma unroll
-    for (int q = 0; q < P; ++q) v[q] = valid ? sub[(tau + TPC * q) * S3 + col] : make_float2(0.f, 0.f);
+    for (int q = 0; q < P; ++q) {
+      const float2* x = sub + (tau + TPC * q) * S3;
+      if (col == 0) {
+        const float2 a = x[0], b = x[M];
+        v[q] = make_float2(a.x - b.y, a.y + b.x);  // a + i b
+      } else {
+        v[q] = valid ? x[col] : make_float2(0.f, 0.f);
+      }
+    }
     fft_core<P, +1>(v, xb, tau, c, C, Q, LQ, twQ, pl.tws, nthr);
     if (valid) {
 #pragma unroll
-      for (int q = 0; q < P; ++q) sub[(tau + TPC * q) * S3 + col] = v[q];
+      for (int q = 0; q < P; ++q) {
+        float2* x = sub + (tau + TPC * q) * S3;
+        if (col == 0) {
+          x[0] = make_float2(v[q].x, 0.f);
+          x[M] = make_float2(v[q].y, 0.f);
+        } else {
+          x[col] = v[q];
+        }
+      }
     }
   }
   __syncthreads();
