@@ -60,6 +60,10 @@ CASES = [
     ((256, 256), (1.0, 1.0), "paper_poly", dict(m=4.0, k=2, l=1, n=2), 1),
     ((8, 16, 4), (1.0, 0.5, 2.0), "matern", dict(ell=0.2, nu=1.5), 2),
     ((32, 32, 32), (1.0, 1.0, 1.0), "gaussian", dict(ell=0.1), 1),
+    # the fixed geometries 2N = 1024, 2048, 4096 (rows and strided launches)
+    ((512, 1024), (1.0, 1.0), "matern", dict(ell=0.05, nu=1.5), 2),
+    ((2048, 64), (2.0, 1.0), "gaussian", dict(ell=0.05), 2),
+    ((2048, 4, 512), (1.0, 0.5, 1.0), "matern", dict(ell=0.1, nu=2.5), 1),
 ]
 
 
