@@ -53,25 +53,42 @@ def _fingerprint() -> str:
 
 
 # The sources behind each kernel kind of the 2-D Algorithm 2 step (its .cu
-# files and the launch code in api.cu; every header counts too): a stored
-# DRAM-traffic figure is valid while their fingerprint is unchanged.
+# files and the launch code in api.cu, with every header they include): a
+# stored DRAM-traffic figure is valid while their fingerprint is unchanged.
 KERNEL_SOURCES = {
     "noise_columns": ("api.cu", "fft_kernels.cu", "spec_noise.cu", "noise_fast.cu", "noise_kernels.cu"),
     "rows_c2r": ("api.cu", "fft_kernels.cu", "spec_other.cu", "c2r_tma.cu"),
 }
 
 
+def _include_closure(files):
+    """The files and every header of this tree they include, transitively."""
+    seen, todo = set(), list(files)
+    while todo:
+        f = todo.pop()
+        if f in seen:
+            continue
+        path = next((os.path.join(d, f) for d in (CSRC, INCLUDE) if os.path.exists(os.path.join(d, f))), None)
+        if path is None:
+            continue
+        seen.add(f)
+        with open(path) as fh:
+            for line in fh:
+                line = line.strip()
+                if line.startswith("#include \""):
+                    todo.append(line.split('"')[1])
+    return sorted(seen)
+
+
 def kernel_fingerprint(kind: str) -> str:
     h = hashlib.sha256()
     h.update(platform.machine().encode())
     h.update(" ".join(ARCH + [f for f in NVCC_FLAGS if not f.startswith("-I")]).encode())
-    own = KERNEL_SOURCES[kind]
-    for d in (CSRC, INCLUDE):
-        for f in sorted(os.listdir(d)):
-            if f.endswith((".cuh", ".h")) or f in own:
-                with open(os.path.join(d, f), "rb") as fh:
-                    h.update(f.encode())
-                    h.update(fh.read())
+    for f in _include_closure(KERNEL_SOURCES[kind]):
+        path = next(os.path.join(d, f) for d in (CSRC, INCLUDE) if os.path.exists(os.path.join(d, f)))
+        with open(path, "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
     return h.hexdigest()
 
 
