@@ -222,6 +222,32 @@ def test_fp32_mixed_fused_passes(case):
     g.close()
 
 
+def test_fp32_mixed_fused_host_delivery_and_plain_form():
+    """The fused mixed-radix passes: grf_sample_host gives the device fields bit
+    for bit, a call of 2 fields on a plan of 5 gives the first 2 of a call of 5,
+    and the plain form of the same plan (GRF_MIXED_FUSED=0) agrees within the
+    FP32 bar (both are checked against the oracle elsewhere)."""
+    import os
+    n = (600, 350)  # 2^3 3 5^2 x 2 5^2 7: radices 3, 5, 5, 8 and 5, 5, 7
+    kw = dict(ell=0.04, nu=1.5)
+    g = _api().GRF(n, (1.0, 1.0), family="matern", precision="fp32", max_batch=5, **kw)
+    d5 = g.sample(seed=21, batch=5).cpu().numpy()
+    d2 = g.sample(seed=21, batch=2).cpu().numpy()
+    h = g.sample_host(seed=21, batch=5).numpy()
+    assert np.array_equal(d5, h)
+    assert np.array_equal(d5[:2], d2)
+    g.close()
+    os.environ["GRF_MIXED_FUSED"] = "0"
+    try:
+        gp = _api().GRF(n, (1.0, 1.0), family="matern", precision="fp32", max_batch=5, **kw)
+        p5 = gp.sample(seed=21, batch=5).cpu().numpy()
+        gp.close()
+    finally:
+        del os.environ["GRF_MIXED_FUSED"]
+    e = np.linalg.norm(p5 - d5) / np.linalg.norm(d5)
+    assert e <= 2 * REL_L2, e
+
+
 def test_fp32_mixed_plan_has_no_adjoint_or_rfft():
     from paper_1105_2737_gb300 import _lib as L
     g = _api().GRF((12, 20), (1.0, 1.0), precision="fp32", max_batch=1)
