@@ -610,13 +610,19 @@ GRF_DEV void fourstep1_body(const FourStepArgs& a, int bx, int64_t bz, int nthr,
 // c and slot C - 1 - c are mirrors.  Each X is drawn once, staged in shared
 // memory, and read back by the thread that forms its mirror's Z.  Y is written
 // with tile T = H (a.T), the second half's run straddling two tiles.
-template <int P>
-GRF_DEV void fourstep1_pair_body(const FourStepArgs& a, int bx, int64_t bz, int nthr, float2* sm) {
-  const int C = a.C, H = C / 2;
+// LB, CC != 0: the transform length B = 2^LB and CC columns per CTA as
+// constants (256 threads).
+template <int P, int LB = 0, int CC = 0>
+GRF_DEV void fourstep1_pair_body(const FourStepArgs& a, int bx, int64_t bz, int nthr_rt, float2* sm) {
+  constexpr bool spec = LB && CC;
+  const int B = spec ? (1 << LB) : a.B;
+  const int logB = spec ? LB : a.logB;
+  const int C = spec ? CC : a.C, H = C / 2;
+  const int nthr = spec ? CC * (1 << LB) / P : nthr_rt;
   const int t = threadIdx.x;
   const int c = t & (C - 1);
   const int tau = t / C;
-  const int TPT = a.B / P;
+  const int TPT = B / P;
   const int half = a.A / 2;
   int k1;
   bool valid;
@@ -632,9 +638,9 @@ GRF_DEV void fourstep1_pair_body(const FourStepArgs& a, int bx, int64_t bz, int 
   const int64_t field = bz;
   const uint64_t key = (a.seed_ptr ? *a.seed_ptr : a.seed) + (uint64_t)(a.zfield ? a.zfield[field] : a.field0 + field);
   const float* stab = a.stab + field * a.stab_zstride;
-  const float* srow = a.stabT + field * a.stabT_zstride + (int64_t)k1 * a.B;  // s_{k1 + A k2} at k2
+  const float* srow = a.stabT + field * a.stabT_zstride + (int64_t)k1 * B;  // s_{k1 + A k2} at k2
   // X of this slot's entries k = k1 + A k2, k2 = tau + TPT q, staged as [c][k2] (pitch B + 1)
-  const int pitch = a.B + 1;
+  const int pitch = B + 1;
   float2 v[P];
 #pragma unroll
   for (int q = 0; q < P; ++q) {
@@ -654,30 +660,36 @@ GRF_DEV void fourstep1_pair_body(const FourStepArgs& a, int bx, int64_t bz, int 
   for (int q = 0; q < P; ++q) {
     const int k2 = tau + TPT * q;
     float2 xm;
-    if (k1 == 0) xm = k2 == 0 ? x1d(a.M, a.M, stab, key, a.trig) : sm[mc * pitch + a.B - k2];
-    else xm = sm[mc * pitch + a.B - 1 - k2];
+    if (k1 == 0) xm = k2 == 0 ? x1d(a.M, a.M, stab, key, a.trig) : sm[mc * pitch + B - k2];
+    else xm = sm[mc * pitch + B - 1 - k2];
     v[q] = c2r_pre(v[q], xm, cmul(wk1, __ldg(a.tw2B + k2)));
   }
-  fft_core<P, +1>(v, sm, tau, c, C, a.B, a.logB, a.twB, a.tws, nthr);
+  fft_core<P, +1>(v, sm, tau, c, C, B, logB, a.twB, a.tws, nthr);
   if (!valid) return;
-  float2* Y = a.Y + field * (int64_t)a.M + ((k1 >> a.logT) * (int64_t)a.B << a.logT) + (k1 & (a.T - 1));
+  float2* Y = a.Y + field * (int64_t)a.M + ((k1 >> a.logT) * (int64_t)B << a.logT) + (k1 & (a.T - 1));
 #pragma unroll
   for (int q = 0; q < P; ++q) {
     // e^{2 pi i x / M}, x = n2 k1 < M, as e^{2 pi i (x >> log B) / A} e^{2 pi i (x mod B) / M}
     const int n2 = tau + TPT * q;
     const int x = n2 * k1;
-    const float2 w = cmul(__ldg(a.twMA + (x >> a.logB)), __ldg(a.twM + (x & (a.B - 1))));
+    const float2 w = cmul(__ldg(a.twMA + (x >> logB)), __ldg(a.twM + (x & (B - 1))));
     Y[(int64_t)n2 << a.logT] = cmul(v[q], w);
   }
 }
 
-template <int P>
-GRF_DEV void fourstep2_body(const FourStepArgs& a, int bx, int64_t bz, int nthr, float2* sm) {
-  const int C = a.C;
+// LA, CC != 0: the transform length A = 2^LA and CC columns per CTA as
+// constants (256 threads).
+template <int P, int LA = 0, int CC = 0>
+GRF_DEV void fourstep2_body(const FourStepArgs& a, int bx, int64_t bz, int nthr_rt, float2* sm) {
+  constexpr bool spec = LA && CC;
+  const int A = spec ? (1 << LA) : a.A;
+  const int logA = spec ? LA : a.logA;
+  const int C = spec ? CC : a.C;
+  const int nthr = spec ? CC * (1 << LA) / P : nthr_rt;
   const int t = threadIdx.x;
   const int c = t & (C - 1);
   const int tau = t / C;
-  const int TPT = a.A / P;
+  const int TPT = A / P;
   const int n2 = bx * C + c;  // < B: C divides B
   const int64_t field = bz;
   const float2* Y = a.Yin + field * (int64_t)a.M + ((int64_t)n2 << a.logT);
@@ -687,7 +699,7 @@ GRF_DEV void fourstep2_body(const FourStepArgs& a, int bx, int64_t bz, int nthr,
     const int k1 = tau + TPT * q;
     v[q] = __ldcg(Y + ((k1 >> a.logT) * (int64_t)a.B << a.logT) + (k1 & (a.T - 1)));
   }
-  fft_core<P, +1>(v, sm, tau, c, C, a.A, a.logA, a.twA, a.tws, nthr);
+  fft_core<P, +1>(v, sm, tau, c, C, A, logA, a.twA, a.tws, nthr);
   float2* o = reinterpret_cast<float2*>(a.zout ? a.zout[field] : a.out + field * (int64_t)a.N);
 #pragma unroll
   for (int q = 0; q < P; ++q) o[n2 + (int64_t)a.B * (tau + TPT * q)] = v[q];

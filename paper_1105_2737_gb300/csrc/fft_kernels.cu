@@ -15,6 +15,7 @@
 // Z[0..M-1] into N = 2M reals with one M-point complex inverse FFT,
 // z = IFFT_M(Z), f[2m] = Re z[m], f[2m+1] = Im z[m].  ROW_R2C is the forward
 // counterpart (pack x[2m] + i x[2m+1], FFT_M, split).
+#include <cstdlib>
 #include "pass_kernels.cuh"
 
 #include <mutex>
@@ -156,6 +157,10 @@ static cudaError_t launch_fourstep_t(int stage, const FourStepArgs& a, int64_t n
 }
 
 cudaError_t launch_fourstep(int stage, int P, const FourStepArgs& a, int64_t nfields, cudaStream_t s) {
+  if (P == 16 && std::getenv("GRF_FOURSTEP_GENERAL") == nullptr) {  // "GRF_FOURSTEP_GENERAL": run-time geometry only
+    cudaError_t e = cudaSuccess;
+    if (launch_fourstep_spec(stage, a, nfields, s, &e)) return e;
+  }
   switch (P) {
     case 16: return launch_fourstep_t<16>(stage, a, nfields, s);
     default: return cudaErrorInvalidValue;  // both factors are >= 16

@@ -128,6 +128,9 @@ cudaError_t build_stab_fourstep(float* stabT, const float* stab, int A, int B, c
 // stage 1, 2, or 3 = stage 1 with mirror-closed column pairs (a.C / 2 pairs per
 // CTA, Y tile a.T = a.C / 2; each X drawn once, see fourstep1_pair_body).
 cudaError_t launch_fourstep(int stage, int P, const FourStepArgs& a, int64_t nfields, cudaStream_t s);
+// The compiled geometries of stages 3 and 2 (fourstep_spec.cu): true if one
+// matched and was launched (its status in *err).
+bool launch_fourstep_spec(int stage, const FourStepArgs& a, int64_t nfields, cudaStream_t s, cudaError_t* err);
 
 // One axis of a Neumann / Dirichlet field (r2r.cu): lines of N + 1 points
 // (N a power of two in [2, 4096]) along an axis of the field array, lines

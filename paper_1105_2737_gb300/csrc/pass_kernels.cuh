@@ -68,16 +68,18 @@ __global__ void __launch_bounds__(256, 3) fourstep_stage1(FourStepArgs a) {
   fourstep1_body<P>(a, blockIdx.x, blockIdx.z, blockDim.x, sm);
 }
 
-template <int P>
+// LN, CC != 0: compile-time transform length 2^LN and CC columns per CTA
+// (fourstep_spec.cu).
+template <int P, int LN = 0, int CC = 0>
 __global__ void __launch_bounds__(256, 3) fourstep_stage1_pair(FourStepArgs a) {
   extern __shared__ float2 sm[];
-  fourstep1_pair_body<P>(a, blockIdx.x, blockIdx.z, blockDim.x, sm);
+  fourstep1_pair_body<P, LN, CC>(a, blockIdx.x, blockIdx.z, blockDim.x, sm);
 }
 
-template <int P>
+template <int P, int LN = 0, int CC = 0>
 __global__ void __launch_bounds__(256, 2) fourstep_stage2(FourStepArgs a) {
   extern __shared__ float2 sm[];
-  fourstep2_body<P>(a, blockIdx.x, blockIdx.z, blockDim.x, sm);
+  fourstep2_body<P, LN, CC>(a, blockIdx.x, blockIdx.z, blockDim.x, sm);
 }
 
 template <int P, int SRC, int MODE, int PAIR, int LN = 0, int CC = 0>
