@@ -24,7 +24,11 @@ __host__ __device__ constexpr size_t plane3_noise_smem_bytes(int N1, int CC) {
 
 template <int LN, int CC, int R>
 __global__ void __launch_bounds__(256, 3) plane3_noise_kernel(ColArgs a, PlaneArgs pl) {
-  constexpr int P = 16, N = 1 << LN, TPT = N / P, NTHR = CC * TPT, U = CC / R, PITCH = N + 1;
+  // The staged columns sit at slot (c mod U) R + c / U with a pitch of N + 16 / CC
+  // float2: a half warp's 64-bit accesses then fall on 16 distinct bank pairs
+  // both when it writes (16 / CC rows of all CC columns) and when it reads the
+  // radix-R inputs (16 / U rows of U consecutive k3).
+  constexpr int P = 16, N = 1 << LN, TPT = N / P, NTHR = CC * TPT, U = CC / R, PITCH = N + 16 / CC;
   static_assert(NTHR == 256 && CC % R == 0, "256-thread geometries, R dividing the columns per CTA");
   extern __shared__ float2 sm[];
   float2* strig = sm + (size_t)(N + N / 16) * CC;
@@ -69,8 +73,9 @@ __global__ void __launch_bounds__(256, 3) plane3_noise_kernel(ColArgs a, PlaneAr
   {
     const int t = CtaCoordsHW{}.tid();
     const int c = t & (CC - 1), tau = t / CC;
+    const int slot = (c % U) * R + c / U;
 #pragma unroll
-    for (int q = 0; q < P; ++q) sm[c * PITCH + tau + TPT * q] = v[q];
+    for (int q = 0; q < P; ++q) sm[slot * PITCH + tau + TPT * q] = v[q];
   }
   __syncthreads();
 
@@ -88,7 +93,7 @@ __global__ void __launch_bounds__(256, 3) plane3_noise_kernel(ColArgs a, PlaneAr
     if (k3 > M) continue;
     float2 x[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) x[r] = sm[(r * U + u) * PITCH + j1];
+    for (int r = 0; r < R; ++r) x[r] = sm[(u * R + r) * PITCH + j1];
     dft_regs<R, +1, 1, 0>(x);  // x[s] = sum_r X_r e^{+2 pi i r s / R}
     float2* dst = wsf + ((int64_t)j1 * R * Q + kp) * S3 + k3;
 #pragma unroll
