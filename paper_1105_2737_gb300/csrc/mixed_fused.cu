@@ -80,8 +80,23 @@ __global__ void __launch_bounds__(512) mixed_c2r_kernel(MixedArgs a) {
   const int jt = blockIdx.x;
   const int t = threadIdx.x, nthr = blockDim.x;
   const float2* ws = a.ws + field * a.ws_stride + (int64_t)jt * ncols * T;
-  // the tile's contiguous run [kd][r] -> bufA[r (M + 1) + kd]
-  for (int idx = t; idx < ncols * T; idx += nthr) bufA[(idx & (T - 1)) * ncols + (idx >> logT)] = __ldcg(ws + idx);
+  // the tile's contiguous run [kd][r] -> bufA[r (M + 1) + kd], eight loads in
+  // flight per thread before they go to shared memory
+  constexpr int U = 8;
+  const int n = ncols * T;
+  for (int i0 = t; i0 < n; i0 += U * nthr) {
+    float2 x[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = i0 + u * nthr;
+      if (idx < n) x[u] = __ldcg(ws + idx);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = i0 + u * nthr;
+      if (idx < n) bufA[(idx & (T - 1)) * ncols + (idx >> logT)] = x[u];
+    }
+  }
   __syncthreads();
   // Z of the c2r split -> bufB[r M + k]
   const float rM = __frcp_rn((float)M);
