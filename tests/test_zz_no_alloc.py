@@ -67,6 +67,28 @@ def test_worst_case_smallest_grids_and_paper_family(L):
         assert rel <= 2e-6 and np.abs(g - ref).max() <= 1e-5 * scale, (c[0], rel)
 
 
+def test_against_the_oracle(L):
+    """Every field of a call against the FP64 oracle directly (not only the
+    plan path): a Matern and a paper-family grid, within the FP32 bar."""
+    import os
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    from oracle import grf_oracle as O
+    calls = [((256, 128), (1.0, 2.0), L.make_spectrum(L.GRF_MATERN, 1.0, 0.05, 1.5),
+              O.Spectrum(O.MATERN, 1.0, 0.05, 1.5), 41, 2),
+             ((64, 128), (8.0, 8.0), L.make_spectrum(L.GRF_PAPER_POLY, 1.0, 0.0, 0.0, 10.0, 1, 2, 1),
+              O.Spectrum(O.PAPER_POLY, 1.0, 0.0, 0.0, 10.0, 1, 2, 1), 17, 2)]
+    for n, Lb, spec, ospec, seed, batch in calls:
+        g = _static(L, n, Lb, spec, seed, batch)
+        for b in range(batch):
+            ref = O.alg2_field(n, Lb, ospec, seed + b)
+            rel = np.linalg.norm(g[b] - ref) / np.linalg.norm(ref)
+            scale = max(1.0, float(np.sqrt((ref ** 2).mean())))
+            assert rel <= 2e-6 and np.abs(g[b] - ref).max() <= 1e-5 * scale, (n, b, rel)
+
+
 def test_sizes_beyond_the_scratch_are_rejected(L):
     out = torch.empty(4, dtype=torch.float32, device="cuda")
     nn = (C.c_int64 * 2)(2048, 64)
