@@ -103,16 +103,17 @@ __global__ void __launch_bounds__(kR2rThreads, kR2rMinBlocks) r2r_line_kernel(R2
       }
       const int64_t j0 = lj0[l];
       const int64_t m = (j0 >> 2) + qi;
-      if (4 * m > j0 + N) continue;
+      const int d = (int)(4 * m - j0);  // position in the line of the call's first point, -3..N + 3
+      if (d > N) continue;
       const u32x4 w = philox_call((uint64_t)m, 2u, lkey[l]);
       const float2 z01 = box_muller(w.x, w.y, a.trig);
       const float2 z23 = box_muller(w.z, w.w, a.trig);
       const float z[4] = {z01.x, z01.y, z23.x, z23.y};
+      const float* tb = a.tab + 4 * m;  // t_K of the call's points
+      const int row = l * W + d;
 #pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        const int64_t j = 4 * m + s;
-        if (j >= j0 && j <= j0 + N) tile[l * W + (int)(j - j0)] = z[s] * __ldg(a.tab + j);
-      }
+      for (int s = 0; s < 4; ++s)
+        if (d + s >= 0 && d + s <= N) tile[row + s] = z[s] * __ldg(tb + s);
     }
   } else if constexpr (SRC == R2R_LOAD_ROWS) {  // contiguous rows
     for (int e = t; e < W * G; e += nthr) {
@@ -183,11 +184,13 @@ __global__ void __launch_bounds__(kR2rThreads, kR2rMinBlocks) r2r_line_kernel(R2
 
   // 4. the tile back to global memory, as it was read
   if constexpr (SRC != R2R_LOAD_STRIDED) {
-    for (int e = t; e < W * G; e += nthr) {
-      const int l = e / W;
-      const int n = e - l * W;
+    for (int l = 0; l < G; ++l) {  // line by line: no division, one base per line
       const int64_t base = lbase[l];
-      if (base >= 0) a.f[(base & (kFaceLine - 1)) + n] = base < kFaceLine ? tile[e] : 0.f;
+      if (base < 0) continue;
+      float* dst = a.f + (base & (kFaceLine - 1));
+      const float* src = tile + l * W;
+      const bool face = base >= kFaceLine;
+      for (int n = t; n < W; n += nthr) dst[n] = face ? 0.f : src[n];
     }
   } else {
     const int E = W * G;
