@@ -328,7 +328,7 @@ def run_ours(args):
     passes = {k: {"launches": len(v), "avg_ms": sum(v) / len(v),
                   "GBps_alg": (_pass_bytes(k, hsize, ntot) * BATCH / (sum(v) / len(v) / 1000.0) / 1e9)
                   if _pass_bytes(k, hsize, ntot) else None} for k, v in per_kind.items()}
-    # BASELINE's per-pass figure: 4 B per point written per HBM pass (P = 2 for 2-D)
+    # the per-pass figure: 4 B per point written per HBM pass (P = 2 for 2-D)
     P = 2
     per_pass_frac = (fields * ntot * 4 * P) / (ms / 1000.0) / 1e9 / peak / ws
     strict_frac = (fields * ntot * 4) / (ms / 1000.0) / 1e9 / peak / ws

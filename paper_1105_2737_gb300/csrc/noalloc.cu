@@ -6,7 +6,7 @@
 // forbidden), and latency-critical loops where cudaMalloc / cudaFree would
 // implicitly synchronise the device.  grf_sample_2d_static serves them: its
 // tables and its intermediate half spectrum live in one file-scope device
-// array, `g_noalloc_scratch`, that the driver reserves when it loads this
+// array, `g_noalloc_scratch`, that the CUDA driver reserves when it loads this
 // library on a device and keeps until the process exits.  The caller passes
 // only the output.
 //
