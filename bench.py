@@ -715,6 +715,8 @@ def run_case(args):
     b = args.batch if args.batch != BATCH else 2
     if args.case == "3d256":
         g = GRF((256, 256, 256), (1.0, 1.0, 1.0), family="gaussian", sigma=1.0, ell=0.03, max_batch=b)
+    elif args.case == "1d2p20":
+        g = GRF((1 << 20,), (1.0,), max_batch=b, **SPEC)
     else:
         g = GRF((3000, 3000), (1.0, 1.0), max_batch=b, **SPEC)
     o = g.empty(b)
@@ -821,9 +823,9 @@ def main():
     ap.add_argument("--study", choices=["cov1d", "bc", "fig3", "mixed"],
                     help="run the paper's 1-D covariance study, or the Neumann / Dirichlet fields, instead")
     ap.add_argument("--study-samples", type=int, default=100_000_000)
-    ap.add_argument("--case", choices=["3d256", "mixed3000"],
+    ap.add_argument("--case", choices=["3d256", "mixed3000", "1d2p20"],
                     help="profiling: two calls of --batch fields of one workload (3-D 256^3 Gaussian ell = 0.03, "
-                         "or 2-D 3000^2 on the fused mixed-radix passes), no timing")
+                         "2-D 3000^2 on the fused mixed-radix passes, or 1-D 2^20 on the four-step), no timing")
     args = ap.parse_args()
     if args.study == "cov1d":
         run_cov1d_study(args)

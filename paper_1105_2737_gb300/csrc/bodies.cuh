@@ -639,8 +639,10 @@ GRF_DEV void fourstep1_pair_body(const FourStepArgs& a, int bx, int64_t bz, int 
   const uint64_t key = (a.seed_ptr ? *a.seed_ptr : a.seed) + (uint64_t)(a.zfield ? a.zfield[field] : a.field0 + field);
   const float* stab = a.stab + field * a.stab_zstride;
   const float* srow = a.stabT + field * a.stabT_zstride + (int64_t)k1 * B;  // s_{k1 + A k2} at k2
-  // X of this slot's entries k = k1 + A k2, k2 = tau + TPT q, staged as [c][k2] (pitch B + 1)
-  const int pitch = B + 1;
+  // X of this slot's entries k = k1 + A k2, k2 = tau + TPT q, staged as [c][k2]
+  // with a pitch of B + 16 / C (C < 16) or B + 1: a half warp (16 / C values of
+  // tau for each of the C slots) then writes and reads 16 distinct bank pairs
+  const int pitch = B + (C < 16 ? 16 / C : 1);
   float2 v[P];
 #pragma unroll
   for (int q = 0; q < P; ++q) {
