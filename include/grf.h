@@ -204,11 +204,11 @@ grf_status grf_sample(grf_plan p, uint64_t seed, int64_t batch, void* out, void*
 /*
  * grf_sample_host - same fields as grf_sample, delivered to host memory.
  *   host_out : host pointer to batch fields.
- * The device computes into plan-owned buffers in chunks while earlier chunks
- * are copied out (each chunk over GRF_COPY_STREAMS copy streams, default 1),
- * so copies overlap compute.  With GRF_HOST_DIRECT=1 and pinned host memory
- * mapped into the device's address space, the kernels write the fields there
- * directly instead.  Returns after the fields are in host memory
+ * Pinned host memory mapped into the device's address space is written by
+ * the kernels directly.  Other host memory (or GRF_HOST_DIRECT=0): the device
+ * computes into plan-owned buffers in chunks while earlier chunks are copied
+ * out (each chunk over GRF_COPY_STREAMS copy streams, default 1), so copies
+ * overlap compute.  Returns after the fields are in host memory
  * (synchronises `stream`).
  */
 grf_status grf_sample_host(grf_plan p, uint64_t seed, int64_t batch, void* host_out, void* stream);
