@@ -28,3 +28,20 @@ def test_reference_arm_prints_one_contract_line():
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_kernel_fingerprints_cover_each_kernels_sources():
+    """The traffic figure of a kernel stays valid while the sources it is built
+    from are unchanged: the fingerprint covers the kernel's .cu files, the
+    launch code and every header they include, and nothing else."""
+    from paper_1105_2737_gb300 import build as B
+    noise = B._include_closure(B.KERNEL_SOURCES["noise_columns"])
+    rows = B._include_closure(B.KERNEL_SOURCES["rows_c2r"])
+    for f in ("noise_fast.cu", "noise_fast.cuh", "common.cuh", "fft_core.cuh", "bodies.cuh", "api.cu", "grf.h"):
+        assert f in noise, f
+    for f in ("spec_other.cu", "c2r_tma.cu", "tma.cuh", "fft_core.cuh", "api.cu"):
+        assert f in rows, f
+    for f in ("r2r.cuh", "r2r.cu", "mixed_fused.cu", "plane3d.cu", "batch.cu"):
+        assert f not in noise and f not in rows, f
+    fp = {k: B.kernel_fingerprint(k) for k in B.KERNEL_SOURCES}
+    assert all(len(v) == 64 for v in fp.values()) and fp["noise_columns"] != fp["rows_c2r"]
