@@ -34,7 +34,8 @@ def test_kernel_fingerprints_cover_each_kernels_sources():
     """The traffic figure of a kernel stays valid while the sources it is built
     from are unchanged: the fingerprint covers the kernel's .cu files, the
     launch code and every header they include, and nothing else."""
-    from paper_1105_2737_gb300 import build as B
+    import importlib
+    B = importlib.import_module("paper_1105_2737_gb300.build")
     noise = B._include_closure(B.KERNEL_SOURCES["noise_columns"])
     rows = B._include_closure(B.KERNEL_SOURCES["rows_c2r"])
     for f in ("noise_fast.cu", "noise_fast.cuh", "common.cuh", "fft_core.cuh", "bodies.cuh", "api.cu", "grf.h"):
